@@ -1,0 +1,228 @@
+/*
+ * gc.h -- C ABI of the GB300 speculative graph-coloring library (libgc.so).
+ *
+ * Distance-1 coloring of an undirected graph G = (V, E): a map C: V -> N with
+ * C(u) != C(v) for every edge (u, v); the number of colors is max_u C(u)
+ * (Sec. 1 of Sariyuce, Saule, Catalyurek, "On Distributed Graph Coloring with
+ * Iterative Recoloring", arXiv 1407.6745).  The library runs, on one GPU:
+ *
+ *   gc_color    speculative rounds (Sec. 2.2): every uncolored vertex picks a
+ *               tentative color -- First Fit (Alg. 1, Sec. 2.1) or Random-X
+ *               Fit (Sec. 3.2) -- then conflicts are detected and the endpoint
+ *               lower in a random total order is uncolored for the next
+ *               round, until no conflict is left;
+ *   gc_recolor  iterative recoloring (Culberson's iterated greedy, Sec. 2.1;
+ *               RC, Sec. 3): the classes of a proper coloring are recolored
+ *               one class after another in a class permutation (RV, NI, ND,
+ *               RAND), each vertex First Fit against the classes already
+ *               recolored; the color count never increases;
+ *   gc_validate the definition of Sec. 1 checked on the device.
+ *
+ * Determinism: results depend only on (graph, arguments, seed), never on
+ * thread scheduling.  Tentative colors are chosen against the colors fixed
+ * before the round; a vertex loses iff a neighbor has the same tentative
+ * color and a larger (priority, id), priority = Philox4x32-10 word 0 of
+ * counter (v_lo, v_hi, 0, 1) under key (seed_lo, seed_hi); Random-X Fit takes
+ * the j-th permissible color (0-based), j = floor(w * X / 2^32), w = Philox
+ * word 0 of counter (v_lo, v_hi, round, 2); RAND shuffles the ascending list
+ * of present colors (Knuth/Fisher-Yates, i = k-1..1, j = floor(w * (i+1) /
+ * 2^32), w = Philox word 0 of counter (i, iteration, 0, 3)).
+ *
+ * Graph layout: symmetric CSR, offsets int64[n+1] with offsets[0] = 0,
+ * non-decreasing, offsets[n] = nnz; idx int32[nnz] neighbor ids in [0, n).
+ * Every undirected edge appears in both rows; duplicates are tolerated.
+ * Colors are int32, 1-based.
+ *
+ * Memory: every pointer argument of a call (graph arrays, colors in and out)
+ * lives in the memory space named by gc_graph.mem: GC_MEM_DEVICE (device
+ * memory of the current CUDA device, e.g. torch tensors) or GC_MEM_HOST
+ * (host memory; the call copies to the device, runs, and copies the result
+ * back; pinned memory makes those copies faster).  Statistics and per-iteration
+ * color counts are always host memory.  The caller owns all buffers; the
+ * library allocates its scratch from its own stream-ordered pool and frees it
+ * before returning.
+ *
+ * Streams and synchronisation: `stream` is a cudaStream_t (NULL = the legacy
+ * default stream).  Work is enqueued on it and every call waits for that
+ * stream before returning, so outputs are ready and device-side errors are
+ * reported by the return value.
+ *
+ * Errors: a call returns GC_OK or an error code and never aborts.  The
+ * kernels bounds-check every offset and neighbor id they read, so a malformed
+ * graph yields GC_ERR_BAD_GRAPH, not a memory fault.  On error the output
+ * contents are unspecified.
+ */
+#ifndef GC_H_
+#define GC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GC_OK = 0,
+    GC_ERR_INVALID_ARG = 1,    /* NULL pointer, n < 0, X < 1, unknown enum   */
+    GC_ERR_BAD_GRAPH = 2,      /* offsets not monotone / out of range, id not in [0, n) */
+    GC_ERR_IMPROPER_INPUT = 3, /* gc_recolor input not a proper coloring     */
+    GC_ERR_OOM = 4,            /* device or pinned host allocation failed    */
+    GC_ERR_CUDA = 5,           /* a CUDA runtime call failed                 */
+    GC_ERR_TIMEOUT = 6,        /* a bounded device-side wait ran out         */
+    GC_ERR_ROUND_LIMIT = 7     /* more than n+1 speculative rounds (cannot happen
+                                  for a valid graph: the top-priority vertex of the
+                                  work set always keeps its color)           */
+} gc_status;
+
+typedef enum { GC_FIRST_FIT = 0, GC_RANDOM_X_FIT = 1 } gc_strategy;
+
+typedef enum {
+    GC_PERM_REVERSE = 0, /* RV: decreasing color                              */
+    GC_PERM_NONINC = 1,  /* NI: non-increasing class size, ties smaller color */
+    GC_PERM_NONDEC = 2,  /* ND: non-decreasing class size, ties smaller color */
+    GC_PERM_RANDOM = 3   /* RAND: seeded Knuth shuffle                        */
+} gc_perm;
+
+typedef enum { GC_MEM_DEVICE = 0, GC_MEM_HOST = 1 } gc_memspace;
+
+/* Symmetric CSR graph (see layout above).  Read-only for the library. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t* offsets; /* n + 1 entries */
+    const int32_t* idx;     /* nnz entries   */
+    int32_t mem;            /* gc_memspace of every pointer argument of the call */
+} gc_graph;
+
+/* Optional statistics (host memory; pass NULL to skip). */
+typedef struct {
+    int32_t rounds;         /* speculative rounds (gc_color)                     */
+    int32_t iterations;     /* recoloring iterations done                        */
+    int32_t max_color;      /* max_v C(v) of the output                          */
+    int32_t reserved;
+    int64_t edges_examined; /* adjacency entries scanned by the hot kernels       */
+    int64_t conflicts;      /* vertices uncolored by conflict resolution, summed  */
+    float ms_color;         /* device time of the speculative coloring            */
+    float ms_recolor;       /* device time of all recoloring iterations           */
+} gc_stats;
+
+/* Result of gc_validate (host memory). */
+typedef struct {
+    int64_t n_conflicts;      /* directed entries (v, u), u in adj(v), C(u) == C(v) */
+    int64_t n_uncolored;      /* vertices with C(v) < 1                               */
+    int32_t max_color;        /* max_v C(v)                                           */
+    int32_t n_distinct;       /* distinct colors >= 1                                 */
+    int64_t first_bad_vertex; /* smallest v uncolored or in a conflict, -1 if none    */
+} gc_validation;
+
+/*
+ * Speculative coloring to convergence (Sec. 2.2 rounds; Alg. 1 First Fit,
+ * Sec. 2.1; Random-X Fit, Sec. 3.2).
+ *   strategy   GC_FIRST_FIT (X ignored, treated as 1) or GC_RANDOM_X_FIT (X >= 1).
+ *   seed       keys the priorities and the Random-X draws.
+ *   colors_out int32[n]: the coloring, each C(v) in [1, deg(v) + X].
+ *   stats      may be NULL.
+ */
+gc_status gc_color(const gc_graph* g, gc_strategy strategy, int32_t X, uint64_t seed,
+                   int32_t* colors_out, gc_stats* stats, void* stream);
+
+/*
+ * Iterative recoloring (Sec. 2.1, Culberson; Sec. 3, RC and the class
+ * permutations).  colors_in must be a proper coloring with colors in
+ * [1, 2^28] (checked: GC_ERR_IMPROPER_INPUT).  iterations >= 0; 0 copies the
+ * input.  seed is used by GC_PERM_RANDOM only.  colors_out may alias
+ * colors_in.  ncolors_per_iter (host, may be NULL) receives iterations + 1
+ * entries: the max color of the input, then after each iteration.
+ */
+gc_status gc_recolor(const gc_graph* g, const int32_t* colors_in, gc_perm perm,
+                     int32_t iterations, uint64_t seed, int32_t* colors_out,
+                     int32_t* ncolors_per_iter, gc_stats* stats, void* stream);
+
+/*
+ * The paper's full method in one call: gc_color followed by `iterations`
+ * recoloring iterations of gc_recolor on its (proper by construction)
+ * output, with no input re-validation and no intermediate host round trip.
+ * Same arguments as the two calls; perm_seed keys GC_PERM_RANDOM.  check
+ * (host, may be NULL) receives gc_validate of the final coloring, computed on
+ * the device before the result is copied out.
+ */
+gc_status gc_color_recolor(const gc_graph* g, gc_strategy strategy, int32_t X, uint64_t seed,
+                           gc_perm perm, int32_t iterations, uint64_t perm_seed,
+                           int32_t* colors_out, int32_t* ncolors_per_iter, gc_stats* stats,
+                           gc_validation* check, void* stream);
+
+/* The random total order of Sec. 2.2 as used by gc_color: out[v] =
+ * prio(v) = Philox4x32-10 word 0 of counter (v_lo, v_hi, 0, 1) under key
+ * (seed_lo, seed_hi), for v in [0, n).  out is device memory (uint32[n]). */
+gc_status gc_priorities(uint64_t seed, int64_t n, uint32_t* out, void* stream);
+
+/* Checks the coloring against the definition of Sec. 1 and the graph's
+ * structure (GC_ERR_BAD_GRAPH if malformed). */
+gc_status gc_validate(const gc_graph* g, const int32_t* colors, gc_validation* out, void* stream);
+
+/* Structure check of a CSR: offsets start at 0, never decrease, end at nnz;
+ * ids in [0, n); no self-loop.  GC_OK or GC_ERR_BAD_GRAPH; first_bad_vertex
+ * (may be NULL) receives the smallest offending row, or -1. */
+gc_status gc_check_graph(const gc_graph* g, int64_t* first_bad_vertex, void* stream);
+
+/*
+ * Scheduling knobs (not part of the method: results are identical for every
+ * setting).  A vertex of degree d with d + X <= 64 is handled by a group of
+ * 4 lanes if d <= g4_max_deg, 8 if d <= g8_max_deg, 16 if d <= g16_max_deg,
+ * else 32; otherwise by one warp with a shared-memory bitmap if
+ * d <= warp_max_deg, else by a whole block.  grid_blocks = 0 picks 8 blocks
+ * per SM.  recolor_mode 0 runs each recoloring iteration as one dataflow
+ * launch (vertices wait, with a bounded spin of spin_limit polls, for their
+ * earlier-class neighbors); 1 launches one grid per color class.  The
+ * setting is process-wide; change it only while no call is running.
+ */
+typedef struct {
+    int32_t g4_max_deg;
+    int32_t g8_max_deg;
+    int32_t g16_max_deg;
+    int32_t warp_max_deg;
+    int32_t grid_blocks;
+    int32_t recolor_mode;
+    int32_t spin_limit;
+    int32_t reserved;
+} gc_tuning;
+
+/* Sets the scheduling knobs (NULL restores the defaults).  GC_ERR_INVALID_ARG
+ * if a threshold is out of order or negative. */
+gc_status gc_set_tuning(const gc_tuning* t);
+/* Reads the knobs in force. */
+gc_status gc_get_tuning(gc_tuning* out);
+
+/* Number of kernel launches the library has made in this process. */
+int64_t gc_kernel_launches(void);
+
+/*
+ * Kernel timing (tracing aid, off by default).  While enabled, the library
+ * brackets each of its kernel launches with CUDA events on the launching
+ * stream and accumulates, per kernel, the launch count and the summed
+ * device time, read back after the calls return.  Enabling resets the
+ * counters.  Not for use inside stream capture.
+ */
+typedef struct {
+    char name[40];
+    int64_t launches;
+    double ms;
+} gc_kernel_time;
+
+void gc_profile_enable(int32_t on);
+/* Copies up to max entries (kernels launched at least once) into out and
+ * returns how many there are. */
+int32_t gc_profile_read(gc_kernel_time* out, int32_t max);
+
+/* Static description of a status code. */
+const char* gc_status_string(gc_status s);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int32_t gc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GC_H_ */

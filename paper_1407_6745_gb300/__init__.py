@@ -1,0 +1,304 @@
+"""GB300 speculative distance-1 graph coloring with iterative recoloring.
+
+Thin Python binding of the C ABI in ``include/gc.h`` (``libgc.so``).  The
+functions carry the C names and only marshal arguments: every step of the
+method runs in the library's CUDA kernels.  Graph and color arrays are torch
+tensors; CUDA tensors are passed as device pointers (``GC_MEM_DEVICE``, on the
+current torch stream), CPU tensors as host pointers (``GC_MEM_HOST``: the
+library copies them to the GPU and back).
+
+There is no CPU fallback: if ``libgc.so`` has not been built (``python -m
+paper_1407_6745_gb300.build``) every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+__all__ = [
+    "GCError", "FIRST_FIT", "RANDOM_X_FIT", "PERM", "library_path", "load",
+    "gc_color", "gc_recolor", "gc_color_recolor", "gc_validate", "gc_check_graph",
+    "gc_priorities", "gc_set_tuning", "gc_get_tuning", "gc_profile_enable", "gc_profile_read",
+    "gc_kernel_launches", "gc_status_string", "gc_version",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libgc.so")
+_lock = threading.Lock()
+_lib = None
+
+FIRST_FIT, RANDOM_X_FIT = 0, 1
+PERM = {"RV": 0, "NI": 1, "ND": 2, "RAND": 3}
+GC_MEM_DEVICE, GC_MEM_HOST = 0, 1
+STATUS = {0: "GC_OK", 1: "GC_ERR_INVALID_ARG", 2: "GC_ERR_BAD_GRAPH", 3: "GC_ERR_IMPROPER_INPUT",
+          4: "GC_ERR_OOM", 5: "GC_ERR_CUDA", 6: "GC_ERR_TIMEOUT", 7: "GC_ERR_ROUND_LIMIT"}
+
+
+class GCError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+        super().__init__(f"{where}: {self.name} ({gc_status_string(code)})")
+
+
+class _Graph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("offsets", ctypes.c_void_p),
+                ("idx", ctypes.c_void_p), ("mem", ctypes.c_int32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("max_color", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("edges_examined", ctypes.c_int64), ("conflicts", ctypes.c_int64),
+                ("ms_color", ctypes.c_float), ("ms_recolor", ctypes.c_float)]
+
+
+class _Validation(ctypes.Structure):
+    _fields_ = [("n_conflicts", ctypes.c_int64), ("n_uncolored", ctypes.c_int64),
+                ("max_color", ctypes.c_int32), ("n_distinct", ctypes.c_int32),
+                ("first_bad_vertex", ctypes.c_int64)]
+
+
+class _KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("g4_max_deg", "g8_max_deg", "g16_max_deg",
+                                               "warp_max_deg", "grid_blocks", "recolor_mode",
+                                               "spin_limit", "reserved")]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libgc.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing; build it with "
+                               "`python -m paper_1407_6745_gb300.build`")
+        lib = ctypes.CDLL(_LIB_PATH)
+        P, G = ctypes.c_void_p, ctypes.POINTER(_Graph)
+        S = ctypes.POINTER(_Stats)
+        lib.gc_color.argtypes = [G, ctypes.c_int, ctypes.c_int32, ctypes.c_uint64, P, S, P]
+        lib.gc_recolor.argtypes = [G, P, ctypes.c_int, ctypes.c_int32, ctypes.c_uint64, P, P, S, P]
+        lib.gc_color_recolor.argtypes = [G, ctypes.c_int, ctypes.c_int32, ctypes.c_uint64,
+                                         ctypes.c_int, ctypes.c_int32, ctypes.c_uint64, P, P, S,
+                                         ctypes.POINTER(_Validation), P]
+        lib.gc_validate.argtypes = [G, P, ctypes.POINTER(_Validation), P]
+        lib.gc_check_graph.argtypes = [G, ctypes.POINTER(ctypes.c_int64), P]
+        lib.gc_priorities.argtypes = [ctypes.c_uint64, ctypes.c_int64, P, P]
+        lib.gc_priorities.restype = ctypes.c_int
+        lib.gc_set_tuning.argtypes = [ctypes.POINTER(_Tuning)]
+        lib.gc_get_tuning.argtypes = [ctypes.POINTER(_Tuning)]
+        for f in ("gc_color", "gc_recolor", "gc_color_recolor", "gc_validate", "gc_check_graph",
+                  "gc_priorities", "gc_set_tuning", "gc_get_tuning"):
+            getattr(lib, f).restype = ctypes.c_int
+        lib.gc_kernel_launches.restype = ctypes.c_int64
+        lib.gc_profile_enable.argtypes = [ctypes.c_int32]
+        lib.gc_profile_read.argtypes = [ctypes.POINTER(_KernelTime), ctypes.c_int32]
+        lib.gc_profile_read.restype = ctypes.c_int32
+        lib.gc_status_string.argtypes = [ctypes.c_int]
+        lib.gc_status_string.restype = ctypes.c_char_p
+        lib.gc_version.restype = ctypes.c_int32
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise GCError(rc, where)
+
+
+def _ptr(t):
+    return None if t is None or t.numel() == 0 else ctypes.c_void_p(t.data_ptr())
+
+
+def _graph(offsets: torch.Tensor, idx: torch.Tensor):
+    if offsets.dtype != torch.int64 or idx.dtype != torch.int32:
+        raise TypeError("offsets must be int64 and idx int32")
+    if offsets.device != idx.device:
+        raise ValueError("offsets and idx must be on the same device")
+    offsets = offsets.contiguous()
+    idx = idx.contiguous()
+    g = _Graph()
+    g.n = offsets.numel() - 1
+    g.nnz = idx.numel()
+    g.offsets = _ptr(offsets)
+    g.idx = _ptr(idx)
+    g.mem = GC_MEM_DEVICE if offsets.is_cuda else GC_MEM_HOST
+    return g, (offsets, idx)
+
+
+def _stream(device: torch.device, stream):
+    if device.type != "cuda":
+        return None
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _stats_dict(st: _Stats):
+    return {k: getattr(st, k) for k, _ in _Stats._fields_ if k != "reserved"}
+
+
+def _strategy(s):
+    if isinstance(s, str):
+        return {"FF": FIRST_FIT, "RXF": RANDOM_X_FIT}[s.upper()]
+    return int(s)
+
+
+def _perm(p):
+    return PERM[p.upper()] if isinstance(p, str) else int(p)
+
+
+def _check_colors(t: torch.Tensor, n: int, device, name: str):
+    if t.dtype != torch.int32 or t.numel() != n or t.device != device or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous int32 tensor of {n} entries on {device}")
+
+
+def gc_color(offsets, idx, strategy="FF", X: int = 1, seed: int = 0, out=None, stream=None):
+    """Speculative coloring (Sec. 2.2 rounds; First Fit or Random-X Fit).
+    Returns (colors int32[n], stats dict)."""
+    lib = load()
+    g, keep = _graph(offsets, idx)
+    dev = keep[0].device
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.int32, device=dev)
+    _check_colors(out, g.n, dev, "out")
+    st = _Stats()
+    _check(lib.gc_color(ctypes.byref(g), _strategy(strategy), int(X), int(seed) & (2**64 - 1),
+                        _ptr(out), ctypes.byref(st), _stream(dev, stream)), "gc_color")
+    return out, _stats_dict(st)
+
+
+def gc_recolor(offsets, idx, colors_in, perm="RV", iterations: int = 1, seed: int = 0, out=None,
+               stream=None):
+    """Iterative recoloring (Sec. 2.1 / Sec. 3).  Returns (colors, ncolors
+    list of iterations + 1 max colors, stats dict)."""
+    lib = load()
+    g, keep = _graph(offsets, idx)
+    dev = keep[0].device
+    _check_colors(colors_in, g.n, dev, "colors_in")
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.int32, device=dev)
+    _check_colors(out, g.n, dev, "out")
+    nc = (ctypes.c_int32 * (iterations + 1))()
+    st = _Stats()
+    _check(lib.gc_recolor(ctypes.byref(g), _ptr(colors_in), _perm(perm), int(iterations),
+                          int(seed) & (2**64 - 1), _ptr(out), nc, ctypes.byref(st),
+                          _stream(dev, stream)), "gc_recolor")
+    return out, list(nc), _stats_dict(st)
+
+
+def gc_color_recolor(offsets, idx, strategy="FF", X: int = 1, seed: int = 0, perm="RV",
+                     iterations: int = 0, perm_seed: int = 0, out=None, validate: bool = False,
+                     stream=None):
+    """Speculative coloring followed by recoloring iterations, in one call.
+    Returns (colors, ncolors list, stats dict, validation dict or None)."""
+    lib = load()
+    g, keep = _graph(offsets, idx)
+    dev = keep[0].device
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.int32, device=dev)
+    _check_colors(out, g.n, dev, "out")
+    nc = (ctypes.c_int32 * (iterations + 1))()
+    st = _Stats()
+    val = _Validation() if validate else None
+    _check(lib.gc_color_recolor(ctypes.byref(g), _strategy(strategy), int(X),
+                                int(seed) & (2**64 - 1), _perm(perm), int(iterations),
+                                int(perm_seed) & (2**64 - 1), _ptr(out), nc, ctypes.byref(st),
+                                ctypes.byref(val) if validate else None, _stream(dev, stream)),
+           "gc_color_recolor")
+    vd = {k: getattr(val, k) for k, _ in _Validation._fields_} if validate else None
+    return out, list(nc), _stats_dict(st), vd
+
+
+def gc_validate(offsets, idx, colors, stream=None):
+    """The definition of Sec. 1 checked on the device."""
+    lib = load()
+    g, keep = _graph(offsets, idx)
+    dev = keep[0].device
+    _check_colors(colors, g.n, dev, "colors")
+    v = _Validation()
+    _check(lib.gc_validate(ctypes.byref(g), _ptr(colors), ctypes.byref(v), _stream(dev, stream)),
+           "gc_validate")
+    return {k: getattr(v, k) for k, _ in _Validation._fields_}
+
+
+def gc_check_graph(offsets, idx, stream=None):
+    """Returns -1 for a well-formed CSR, else the first bad row."""
+    lib = load()
+    g, keep = _graph(offsets, idx)
+    first = ctypes.c_int64(-1)
+    rc = lib.gc_check_graph(ctypes.byref(g), ctypes.byref(first), _stream(keep[0].device, stream))
+    if rc not in (0, 2):
+        _check(rc, "gc_check_graph")
+    return int(first.value)
+
+
+def gc_priorities(seed: int, n: int, device="cuda", stream=None):
+    """prio(v) for v in [0, n): the random total order of Sec. 2.2 (uint32
+    values returned in an int64 tensor)."""
+    lib = load()
+    dev = torch.device(device)
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    _check(lib.gc_priorities(int(seed) & (2**64 - 1), int(n), _ptr(out), _stream(dev, stream)),
+           "gc_priorities")
+    return out.to(torch.int64) & 0xFFFFFFFF
+
+
+def gc_set_tuning(**knobs):
+    """Set scheduling knobs (see gc_tuning in gc.h); no arguments restores defaults."""
+    lib = load()
+    if not knobs:
+        _check(lib.gc_set_tuning(None), "gc_set_tuning")
+        return
+    t = _Tuning()
+    _check(lib.gc_get_tuning(ctypes.byref(t)), "gc_get_tuning")
+    for k, v in knobs.items():
+        setattr(t, k, int(v))
+    _check(lib.gc_set_tuning(ctypes.byref(t)), "gc_set_tuning")
+
+
+def gc_get_tuning():
+    lib = load()
+    t = _Tuning()
+    _check(lib.gc_get_tuning(ctypes.byref(t)), "gc_get_tuning")
+    return {k: getattr(t, k) for k, _ in _Tuning._fields_ if k != "reserved"}
+
+
+def gc_profile_enable(on: bool = True):
+    """Per-kernel CUDA-event timing inside the library (resets the totals)."""
+    load().gc_profile_enable(1 if on else 0)
+
+
+def gc_profile_read():
+    """{kernel name: (launches, total ms)} since gc_profile_enable."""
+    lib = load()
+    cnt = lib.gc_profile_read(None, 0)
+    arr = (_KernelTime * max(cnt, 1))()
+    cnt = lib.gc_profile_read(arr, cnt)
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms)) for i in range(cnt)}
+
+
+def gc_kernel_launches() -> int:
+    return int(load().gc_kernel_launches())
+
+
+def gc_status_string(code: int) -> str:
+    return load().gc_status_string(int(code)).decode()
+
+
+def gc_version() -> int:
+    return int(load().gc_version())

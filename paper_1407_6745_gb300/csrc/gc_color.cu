@@ -1,0 +1,422 @@
+// gc_color.cu -- speculative distance-1 coloring on one GPU.
+//
+// The rounds of Sec. 2.2 in a data-parallel (Jacobi) form: in round r every
+// vertex of the work set W_r chooses a tentative color against the colors
+// fixed before the round (First Fit, Alg. 1 / Sec. 2.1, or Random-X Fit,
+// Sec. 3.2); then every vertex of W_r compares its tentative color with its
+// neighbors' and loses if one of them has the same color and a larger
+// (priority, id) -- the random total order of Sec. 2.2.  Winners keep their
+// color, losers form W_{r+1}.  The vertex of W_r with the largest (priority,
+// id) always wins, so the loop ends within |V| rounds.
+//
+// Layout in HBM: colors int32[n] (the output, 0 = uncolored), tent int32[n],
+// prio uint32[n] (Philox, once per call), two work lists int32[n] used as
+// ping-pong buffers, each cut into six degree-bucket regions whose starts are
+// fixed in round 0 (a loser stays in its bucket, so a region never
+// overflows).  All per-round state (round number, bucket counts) lives in a
+// small device control block, so a round's two launches take no host input.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "gc_internal.h"
+
+namespace gc {
+
+struct SpecCtrl {
+    int32_t cnt[2][kNB];    // bucket counts of the work list of parity p
+    int32_t start[kNB];     // region starts (fixed)
+    int32_t init_cnt[kNB];  // round-0 bucket sizes
+    int32_t round;
+    int32_t active;         // |W| for the coming round
+    int32_t max_color;
+    int32_t max_deg;
+    uint32_t err;
+    uint32_t done_blocks;
+    unsigned long long edges;
+    unsigned long long conflicts;
+};
+
+struct SpecArgs {
+    Graph g;
+    int32_t X;
+    uint64_t seed;
+    Tuning tune;
+    int32_t* color;   // fixed colors (0 = in the work set)
+    int32_t* tent;    // tentative colors
+    uint32_t* prio;   // priorities
+    uint8_t* bucket;  // degree bucket per vertex
+    int32_t* list0;
+    int32_t* list1;
+    SpecCtrl* ctrl;
+};
+
+// ---------------------------------------------------------------------------
+// Set-up: priorities, bucket sizes, then the round-0 work list (all vertices)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_spec_setup(SpecArgs a) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kBlock;
+    int32_t my_max_deg = 0;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; i < a.g.n; i += stride) {
+        const int32_t v = static_cast<int32_t>(i);
+        int64_t beg, end;
+        row_range(a.g, v, beg, end, &a.ctrl->err);
+        const int64_t deg = end - beg;
+        my_max_deg = max(my_max_deg, static_cast<int32_t>(deg < INT32_MAX ? deg : INT32_MAX));
+        const int b = bucket_of(deg, a.X, a.tune);
+        a.bucket[v] = static_cast<uint8_t>(b);
+        a.prio[v] = prio_of(a.seed, v);
+        a.color[v] = 0;
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, b);
+        const int leader = __ffs(peers) - 1;
+        if (lane_id() == leader) atomicAdd(&a.ctrl->init_cnt[b], __popc(peers));
+    }
+    warp_max(&a.ctrl->max_deg, my_max_deg);
+}
+
+__global__ void __launch_bounds__(kBlock) k_spec_fill(SpecArgs a) {
+    __shared__ int32_t s_start[kNB];
+    if (threadIdx.x == 0) {
+        int32_t acc = 0;
+        for (int b = 0; b < kNB; ++b) {
+            s_start[b] = acc;
+            acc += a.ctrl->init_cnt[b];
+        }
+        if (blockIdx.x == 0) {
+            for (int b = 0; b < kNB; ++b) a.ctrl->start[b] = s_start[b];
+            a.ctrl->active = acc;
+        }
+    }
+    __syncthreads();
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kBlock;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; i < a.g.n; i += stride) {
+        const int32_t v = static_cast<int32_t>(i);
+        const int b = a.bucket[v];
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, b);
+        const int leader = __ffs(peers) - 1;
+        int32_t base = 0;
+        if (lane_id() == leader) base = atomicAdd(&a.ctrl->cnt[0][b], __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        a.list0[s_start[b] + base + __popc(peers & ((1u << lane_id()) - 1u))] = v;
+    }
+}
+
+// Tile bookkeeping of one round, loaded by every block at kernel start.
+struct RoundTiles {
+    int32_t cnt[kNB];
+    int32_t start[kNB];
+    int32_t prefix[kNB + 1];
+};
+
+__device__ __forceinline__ void load_round_tiles(const SpecCtrl* c, int par, RoundTiles& rt) {
+    if (threadIdx.x == 0) {
+        int32_t acc = 0;
+        for (int b = 0; b < kNB; ++b) {
+            rt.cnt[b] = c->cnt[par][b];
+            rt.start[b] = c->start[b];
+            rt.prefix[b] = acc;
+            acc += (rt.cnt[b] + bucket_tile(b) - 1) / bucket_tile(b);
+        }
+        rt.prefix[kNB] = acc;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int tile_bucket(const RoundTiles& rt, int32_t t) {
+    int b = 0;
+    while (t >= rt.prefix[b + 1]) ++b;
+    return b;
+}
+
+union SpecShared {
+    BlockScratch blk;
+    uint32_t warp_bm[kWarps][kWarpBitmapWords];
+};
+
+// ---------------------------------------------------------------------------
+// Tentative coloring of W_r against the snapshot `color`
+// ---------------------------------------------------------------------------
+template <int G, bool kRXF>
+__device__ __forceinline__ void tentative_group_tile(const SpecArgs& a, const RoundTiles& rt,
+                                                     const int32_t* list, int b, int32_t first,
+                                                     int32_t round, unsigned long long& edges) {
+    const int gi = threadIdx.x / G, gl = threadIdx.x % G;
+    const int32_t k = first + gi;
+    const bool valid = k < rt.cnt[b];
+    int32_t v = 0;
+    int64_t beg = 0, end = 0;
+    uint32_t j = 0;
+    if (valid) {
+        v = list[rt.start[b] + k];
+        row_range(a.g, v, beg, end, &a.ctrl->err);
+        if (kRXF) j = scale_index(rxf_word(a.seed, v, round), static_cast<uint32_t>(a.X));
+    }
+    const int32_t* color = a.color;
+    auto fetch = [color](int32_t u) { return __ldg(color + u); };
+    const int32_t c = choose_reg<G>(a.g, beg, end, gl, j, fetch, &a.ctrl->err);
+    if (valid && gl == 0) {
+        a.tent[v] = c;
+        edges += static_cast<unsigned long long>(end - beg);
+    }
+}
+
+template <bool kRXF>
+__global__ void __launch_bounds__(kBlock) k_tentative(SpecArgs a) {
+    __shared__ SpecShared sm;
+    __shared__ RoundTiles rt;
+    const int32_t round = a.ctrl->round;
+    const int par = round & 1;
+    const int32_t* list = par ? a.list1 : a.list0;
+    if (blockIdx.x == 0 && threadIdx.x < kNB) a.ctrl->cnt[par ^ 1][threadIdx.x] = 0;
+    load_round_tiles(a.ctrl, par, rt);
+    unsigned long long edges = 0;
+    const int32_t* color = a.color;
+    auto fetch = [color](int32_t u) { return __ldg(color + u); };
+    for (int32_t t = blockIdx.x; t < rt.prefix[kNB]; t += gridDim.x) {
+        const int b = tile_bucket(rt, t);
+        const int32_t first = (t - rt.prefix[b]) * bucket_tile(b);
+        switch (b) {
+        case 0: {
+            const int32_t v = list[rt.start[0] + first];
+            int64_t beg, end;
+            row_range(a.g, v, beg, end, &a.ctrl->err);
+            const uint32_t j = kRXF ? scale_index(rxf_word(a.seed, v, round), a.X) : 0u;
+            const int32_t c = choose_block(a.g, beg, end, j, fetch, sm.blk, &a.ctrl->err);
+            if (threadIdx.x == 0) {
+                a.tent[v] = c;
+                edges += static_cast<unsigned long long>(end - beg);
+            }
+            break;
+        }
+        case 1: {
+            const int w = threadIdx.x >> 5;
+            const int32_t k = first + w;
+            if (k < rt.cnt[1]) {
+                const int32_t v = list[rt.start[1] + k];
+                int64_t beg, end;
+                row_range(a.g, v, beg, end, &a.ctrl->err);
+                const uint32_t j = kRXF ? scale_index(rxf_word(a.seed, v, round), a.X) : 0u;
+                const int32_t c = choose_warp(a.g, beg, end, j, fetch, sm.warp_bm[w], &a.ctrl->err);
+                if (lane_id() == 0) {
+                    a.tent[v] = c;
+                    edges += static_cast<unsigned long long>(end - beg);
+                }
+            }
+            break;
+        }
+        case 2: tentative_group_tile<32, kRXF>(a, rt, list, 2, first, round, edges); break;
+        case 3: tentative_group_tile<16, kRXF>(a, rt, list, 3, first, round, edges); break;
+        case 4: tentative_group_tile<8, kRXF>(a, rt, list, 4, first, round, edges); break;
+        default: tentative_group_tile<4, kRXF>(a, rt, list, 5, first, round, edges); break;
+        }
+    }
+    warp_add(&a.ctrl->edges, edges);
+}
+
+// ---------------------------------------------------------------------------
+// Conflict detection; winners fix their color, losers go to W_{r+1}
+// ---------------------------------------------------------------------------
+// u beats v in the total order: larger priority, then larger id
+__device__ __forceinline__ bool beats(uint32_t pu, int32_t u, uint32_t pv, int32_t v) {
+    return pu > pv || (pu == pv && u > v);
+}
+
+template <int G>
+__device__ __forceinline__ bool loses(const SpecArgs& a, int32_t v, int64_t beg, int64_t end,
+                                      int gl) {
+    bool lose = false;
+    if (end > beg) {
+        const int32_t tv = __ldg(a.tent + v);
+        const uint32_t pv = __ldg(a.prio + v);
+        for (int64_t e = beg + gl; e < end && !lose; e += G) {
+            const int32_t u = load_nbr(a.g, e, &a.ctrl->err);
+            if (u < 0 || u == v) continue;
+            if (__ldg(a.tent + u) == tv && beats(__ldg(a.prio + u), u, pv, v)) lose = true;
+        }
+    }
+    return lose;
+}
+
+template <int G>
+__device__ __forceinline__ void conflict_group_tile(const SpecArgs& a, const RoundTiles& rt,
+                                                    const int32_t* list, int32_t* next, int par,
+                                                    int b, int32_t first, int32_t& my_max,
+                                                    unsigned long long& edges) {
+    const int gi = threadIdx.x / G, gl = threadIdx.x % G;
+    const int32_t k = first + gi;
+    const bool valid = k < rt.cnt[b];
+    int32_t v = 0;
+    int64_t beg = 0, end = 0;
+    if (valid) {
+        v = list[rt.start[b] + k];
+        row_range(a.g, v, beg, end, &a.ctrl->err);
+    }
+    const bool lose = group_any<G>(loses<G>(a, v, beg, end, gl));
+    const bool leader = valid && gl == 0;
+    if (leader) {
+        edges += static_cast<unsigned long long>(end - beg);
+        if (!lose) {
+            const int32_t c = __ldg(a.tent + v);
+            a.color[v] = c;
+            my_max = max(my_max, c);
+        }
+    }
+    warp_append(leader && lose, v, &a.ctrl->cnt[par ^ 1][b], next, rt.start[b]);
+}
+
+__global__ void __launch_bounds__(kBlock) k_conflict(SpecArgs a) {
+    __shared__ RoundTiles rt;
+    __shared__ bool s_last;
+    const int32_t round = a.ctrl->round;
+    const int par = round & 1;
+    const int32_t* list = par ? a.list1 : a.list0;
+    int32_t* next = par ? a.list0 : a.list1;
+    load_round_tiles(a.ctrl, par, rt);
+    unsigned long long edges = 0;
+    int32_t my_max = 0;
+    for (int32_t t = blockIdx.x; t < rt.prefix[kNB]; t += gridDim.x) {
+        const int b = tile_bucket(rt, t);
+        const int32_t first = (t - rt.prefix[b]) * bucket_tile(b);
+        switch (b) {
+        case 0: {
+            const int32_t v = list[rt.start[0] + first];
+            int64_t beg, end;
+            row_range(a.g, v, beg, end, &a.ctrl->err);
+            const bool lose = __syncthreads_or(loses<kBlock>(a, v, beg, end, threadIdx.x));
+            if (threadIdx.x == 0) {
+                edges += static_cast<unsigned long long>(end - beg);
+                if (lose) {
+                    const int32_t pos = atomicAdd(&a.ctrl->cnt[par ^ 1][0], 1);
+                    next[rt.start[0] + pos] = v;
+                } else {
+                    const int32_t c = a.tent[v];
+                    a.color[v] = c;
+                    my_max = max(my_max, c);
+                }
+            }
+            break;
+        }
+        case 1:
+        case 2: conflict_group_tile<32>(a, rt, list, next, par, b, first, my_max, edges); break;
+        case 3: conflict_group_tile<16>(a, rt, list, next, par, 3, first, my_max, edges); break;
+        case 4: conflict_group_tile<8>(a, rt, list, next, par, 4, first, my_max, edges); break;
+        default: conflict_group_tile<4>(a, rt, list, next, par, 5, first, my_max, edges); break;
+        }
+    }
+    warp_add(&a.ctrl->edges, edges);
+    warp_max(&a.ctrl->max_color, my_max);
+
+    // The last block to finish closes the round.
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.ctrl->done_blocks, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        volatile SpecCtrl* c = a.ctrl;
+        int32_t total = 0;
+        for (int b = 0; b < kNB; ++b) total += c->cnt[par ^ 1][b];
+        c->active = total;
+        c->conflicts += static_cast<unsigned long long>(total);
+        c->round = round + 1;
+        c->done_blocks = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_priorities(uint64_t seed, int64_t n, uint32_t* out) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kBlock;
+    for (int64_t v = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; v < n; v += stride)
+        out[v] = prio_of(seed, static_cast<int32_t>(v));
+}
+
+gc_status priorities_device(uint64_t seed, int64_t n, uint32_t* out, cudaStream_t s) {
+    if (n == 0) return GC_OK;
+    const int grid = static_cast<int>(std::min<int64_t>((n + kBlock - 1) / kBlock,
+                                                        persistent_grid(current_tuning())));
+    GC_LAUNCH(KID_PRIORITIES, s, k_priorities<<<grid, kBlock, 0, s>>>(seed, n, out));
+    return cuda_status(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------
+// Host driver
+// ---------------------------------------------------------------------------
+namespace {
+struct PinnedWord {
+    int32_t* p = nullptr;
+    PinnedWord() { cudaMallocHost(&p, sizeof(int32_t) * 16); }
+};
+thread_local PinnedWord t_pinned;
+}  // namespace
+
+gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors_out,
+                       gc_stats* stats, cudaStream_t s) {
+    if (g.n == 0) {
+        if (stats) { std::memset(stats, 0, sizeof(*stats)); }
+        return GC_OK;
+    }
+    if (!t_pinned.p) return GC_ERR_OOM;
+    const int64_t n = g.n;
+    Scratch sc_tent, sc_prio, sc_l0, sc_l1, sc_bucket, sc_ctrl;
+    if (!sc_tent.alloc(n * 4, s) || !sc_prio.alloc(n * 4, s) || !sc_l0.alloc(n * 4, s) ||
+        !sc_l1.alloc(n * 4, s) || !sc_bucket.alloc(n, s) || !sc_ctrl.alloc(sizeof(SpecCtrl), s))
+        return GC_ERR_OOM;
+    SpecArgs a;
+    a.g = g;
+    a.X = X;
+    a.seed = seed;
+    a.tune = current_tuning();
+    a.color = colors_out;
+    a.tent = sc_tent.as<int32_t>();
+    a.prio = sc_prio.as<uint32_t>();
+    a.bucket = sc_bucket.as<uint8_t>();
+    a.list0 = sc_l0.as<int32_t>();
+    a.list1 = sc_l1.as<int32_t>();
+    a.ctrl = sc_ctrl.as<SpecCtrl>();
+
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    cudaMemsetAsync(a.ctrl, 0, sizeof(SpecCtrl), s);
+    const int grid = persistent_grid(a.tune);
+    const int setup_grid = static_cast<int>(std::min<int64_t>((n + kBlock - 1) / kBlock, grid));
+    GC_LAUNCH(KID_SPEC_SETUP, s, k_spec_setup<<<setup_grid, kBlock, 0, s>>>(a));
+    GC_LAUNCH(KID_SPEC_FILL, s, k_spec_fill<<<setup_grid, kBlock, 0, s>>>(a));
+    gc_status st = GC_OK;
+    int32_t rounds = 0;
+    for (;;) {
+        if (X > 1) GC_LAUNCH(KID_TENTATIVE, s, k_tentative<true><<<grid, kBlock, 0, s>>>(a));
+        else GC_LAUNCH(KID_TENTATIVE, s, k_tentative<false><<<grid, kBlock, 0, s>>>(a));
+        GC_LAUNCH(KID_CONFLICT, s, k_conflict<<<grid, kBlock, 0, s>>>(a));
+        ++rounds;
+        cudaMemcpyAsync(t_pinned.p, &a.ctrl->active, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        cudaError_t ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) { st = cuda_status(ce); break; }
+        if (t_pinned.p[0] == 0) break;
+        if (rounds > n + 1) { st = GC_ERR_ROUND_LIMIT; break; }
+    }
+    cudaEventRecord(e1, s);
+    SpecCtrl h;
+    cudaError_t ce = cudaMemcpyAsync(&h, a.ctrl, sizeof(SpecCtrl), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess && st == GC_OK) st = cuda_status(ce);
+    if (st == GC_OK) st = status_from_err_bits(h.err);
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->rounds = h.round;
+        stats->max_color = h.max_color;
+        stats->edges_examined = static_cast<int64_t>(h.edges);
+        stats->conflicts = static_cast<int64_t>(h.conflicts);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        stats->ms_color = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+}  // namespace gc

@@ -1,0 +1,366 @@
+// gc_common.cuh -- device building blocks shared by the coloring kernels.
+//
+// Degree-bucketed scheduling: every vertex to (re)color is handled by a group
+// of lanes sized to its degree.  A vertex whose answer is known to lie in the
+// first 64 colors (deg + X <= 64: at most deg colors are forbidden, and the
+// pick is among the first X permissible ones) keeps its forbidden set in a
+// 64-bit register mask, OR-reduced over a group of 4, 8, 16 or 32 lanes; a
+// larger one uses a bitmap in shared memory, per warp (deg <= warp_max_deg)
+// or per block.  The color picked is the j-th clear bit of the mask (First
+// Fit: j = 0), located with popc/ffs.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gc {
+
+constexpr int kBlock = 256;          // threads per block, every kernel
+constexpr int kWarps = kBlock / 32;
+constexpr int kNB = 6;               // degree buckets
+// bucket b: 0 block/vertex, 1 warp/vertex + smem bitmap, 2..5 group of
+// 32/16/8/4 lanes per vertex with a 64-bit register mask
+__host__ __device__ constexpr int bucket_group(int b) {
+    return b == 0 ? kBlock : b == 1 ? 32 : b == 2 ? 32 : b == 3 ? 16 : b == 4 ? 8 : 4;
+}
+// vertices per block tile
+__host__ __device__ constexpr int bucket_tile(int b) {
+    return b == 0 ? 1 : kBlock / bucket_group(b);
+}
+constexpr int kWarpBitmapWords = 64;    // 2048 colors per window, per warp
+constexpr int kBlockBitmapWords = 4096; // 131072 colors per window, per block
+
+// error bits accumulated on the device
+constexpr uint32_t kErrBadGraph = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrImproper = 4u;
+
+// Scheduling thresholds (runtime; tuned per workload).
+struct Tuning {
+    int32_t g4_max_deg;    // deg <= this -> 4 lanes
+    int32_t g8_max_deg;    // -> 8 lanes
+    int32_t g16_max_deg;   // -> 16 lanes
+    int32_t warp_max_deg;  // deg + X > 64 and deg <= this -> warp + smem bitmap
+    int32_t grid_blocks;   // persistent grid size (0 = 8 per SM)
+    int32_t recolor_mode;  // 0 = dataflow (one launch), 1 = one launch per class
+    int32_t spin_limit;    // bounded wait iterations in the dataflow recolor
+    int32_t reserved;
+};
+
+__host__ __device__ inline int bucket_of(int64_t deg, int32_t X, const Tuning& t) {
+    if (deg + (int64_t)X <= 64) {
+        if (deg <= t.g4_max_deg) return 5;
+        if (deg <= t.g8_max_deg) return 4;
+        if (deg <= t.g16_max_deg) return 3;
+        return 2;
+    }
+    return deg <= t.warp_max_deg ? 1 : 0;
+}
+
+struct Graph {
+    const int64_t* off;
+    const int32_t* idx;
+    int32_t n;
+    int64_t nnz;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11), word 0 only.  Device copy written for
+// this library; the key is bumped by the two Weyl constants after each round.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t philox_word0(uint64_t seed, uint32_t x0, uint32_t x1,
+                                                 uint32_t x2, uint32_t x3) {
+    uint32_t key_lo = static_cast<uint32_t>(seed);
+    uint32_t key_hi = static_cast<uint32_t>(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t a_hi = __umulhi(0xD2511F53u, x0), a_lo = 0xD2511F53u * x0;
+        const uint32_t b_hi = __umulhi(0xCD9E8D57u, x2), b_lo = 0xCD9E8D57u * x2;
+        const uint32_t y0 = b_hi ^ x1 ^ key_lo;
+        const uint32_t y2 = a_hi ^ x3 ^ key_hi;
+        x0 = y0;
+        x1 = b_lo;
+        x2 = y2;
+        x3 = a_lo;
+        key_lo += 0x9E3779B9u;
+        key_hi += 0xBB67AE85u;
+    }
+    return x0;
+}
+
+__device__ __forceinline__ uint32_t prio_of(uint64_t seed, int32_t v) {
+    return philox_word0(seed, static_cast<uint32_t>(v), 0u, 0u, 1u);
+}
+__device__ __forceinline__ uint32_t rxf_word(uint64_t seed, int32_t v, int32_t round) {
+    return philox_word0(seed, static_cast<uint32_t>(v), 0u, static_cast<uint32_t>(round), 2u);
+}
+__device__ __forceinline__ uint32_t perm_word(uint64_t seed, int32_t i, int32_t iteration) {
+    return philox_word0(seed, static_cast<uint32_t>(i), static_cast<uint32_t>(iteration), 0u, 3u);
+}
+// index in [0, m) from a 32-bit word: floor(w * m / 2^32)
+__device__ __forceinline__ uint32_t scale_index(uint32_t w, uint32_t m) {
+    return static_cast<uint32_t>((static_cast<uint64_t>(w) * m) >> 32);
+}
+
+// ---------------------------------------------------------------------------
+// Warp / group helpers
+// ---------------------------------------------------------------------------
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+template <int G>
+__device__ __forceinline__ uint64_t group_or(uint64_t m) {
+    uint32_t lo = static_cast<uint32_t>(m), hi = static_cast<uint32_t>(m >> 32);
+    if constexpr (G == 32) {
+        lo = __reduce_or_sync(kFull, lo);
+        hi = __reduce_or_sync(kFull, hi);
+    } else {
+#pragma unroll
+        for (int d = G / 2; d >= 1; d >>= 1) {
+            lo |= __shfl_xor_sync(kFull, lo, d);
+            hi |= __shfl_xor_sync(kFull, hi, d);
+        }
+    }
+    return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+
+template <int G>
+__device__ __forceinline__ bool group_any(bool p) {
+    const uint32_t b = __ballot_sync(kFull, p);
+    if constexpr (G == 32) {
+        return b != 0;
+    } else {
+        const int shift = lane_id() & ~(G - 1);
+        const uint32_t gm = (G == 32) ? kFull : ((1u << G) - 1u);
+        return ((b >> shift) & gm) != 0;
+    }
+}
+
+__device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t x) {
+    const int l = lane_id();
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, d);
+        if (l >= d) x += y;
+    }
+    return x;
+}
+
+// Position (0-based) of the j-th set bit of x; requires j < popc(x).
+__device__ __forceinline__ int select_bit32(uint32_t x, uint32_t j) {
+    int pos = 0;
+    uint32_t c = __popc(x & 0xFFFFu);
+    if (j >= c) { j -= c; x >>= 16; pos += 16; }
+    c = __popc(x & 0xFFu);
+    if (j >= c) { j -= c; x >>= 8; pos += 8; }
+    c = __popc(x & 0xFu);
+    if (j >= c) { j -= c; x >>= 4; pos += 4; }
+    c = __popc(x & 0x3u);
+    if (j >= c) { j -= c; x >>= 2; pos += 2; }
+    c = x & 1u;
+    if (j >= c) pos += 1;
+    return pos;
+}
+
+__device__ __forceinline__ int select_bit64(uint64_t x, uint32_t j) {
+    const uint32_t lo = static_cast<uint32_t>(x);
+    const uint32_t pl = __popc(lo);
+    if (j < pl) return select_bit32(lo, j);
+    return 32 + select_bit32(static_cast<uint32_t>(x >> 32), j - pl);
+}
+
+// Adjacency range of v with the structure checks that keep every later load
+// in bounds: a bad row is flagged and treated as empty.
+__device__ __forceinline__ void row_range(const Graph& g, int32_t v, int64_t& beg, int64_t& end,
+                                          uint32_t* err) {
+    beg = __ldg(g.off + v);
+    end = __ldg(g.off + v + 1);
+    if (beg < 0 || end < beg || end > g.nnz) {
+        atomicOr(err, kErrBadGraph);
+        beg = end = 0;
+    }
+}
+
+__device__ __forceinline__ int32_t load_nbr(const Graph& g, int64_t e, uint32_t* err) {
+    const int32_t u = __ldg(g.idx + e);
+    if (static_cast<uint32_t>(u) >= static_cast<uint32_t>(g.n)) {
+        atomicOr(err, kErrBadGraph);
+        return -1;
+    }
+    return u;
+}
+
+// ---------------------------------------------------------------------------
+// Color choice: the j-th (0-based) color >= 1 not returned by fetch(u) for a
+// neighbor u.  fetch returns the neighbor's color, or a value < 1 to ignore it.
+// ---------------------------------------------------------------------------
+
+// Register path, G lanes per vertex; requires deg + j < 64.  All 32 lanes of
+// the warp must call it (lanes without a vertex pass an empty range).
+template <int G, class Fetch>
+__device__ __forceinline__ int32_t choose_reg(const Graph& g, int64_t beg, int64_t end, int gl,
+                                              uint32_t j, Fetch& fetch, uint32_t* err) {
+    uint64_t m = 0;
+    for (int64_t e = beg + gl; e < end; e += G) {
+        const int32_t u = load_nbr(g, e, err);
+        if (u < 0) continue;
+        const int32_t c = fetch(u);
+        if (static_cast<uint32_t>(c - 1) < 64u) m |= 1ull << (c - 1);
+    }
+    m = group_or<G>(m);
+    const uint64_t free_bits = ~m;
+    if (j == 0) return __ffsll(static_cast<long long>(free_bits));
+    return select_bit64(free_bits, j) + 1;
+}
+
+// Warp path with a 64-word shared bitmap (2048 colors per window); windows
+// advance until the j-th permissible color is found.  Whole warp, one vertex.
+template <class Fetch>
+__device__ __forceinline__ int32_t choose_warp(const Graph& g, int64_t beg, int64_t end,
+                                               uint32_t j, Fetch& fetch, uint32_t* bm,
+                                               uint32_t* err) {
+    const int l = lane_id();
+    int32_t base = 1;
+    for (;;) {
+        bm[l] = 0u;
+        bm[l + 32] = 0u;
+        __syncwarp();
+        for (int64_t e = beg + l; e < end; e += 32) {
+            const int32_t u = load_nbr(g, e, err);
+            if (u < 0) continue;
+            const int32_t c = fetch(u);
+            const uint32_t d = static_cast<uint32_t>(c - base);
+            if (c > 0 && d < 32u * kWarpBitmapWords) atomicOr(&bm[d >> 5], 1u << (d & 31));
+        }
+        __syncwarp();
+        const uint32_t w0 = ~bm[2 * l], w1 = ~bm[2 * l + 1];
+        const uint32_t cnt = __popc(w0) + __popc(w1);
+        const uint32_t incl = warp_inclusive_scan(cnt);
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        if (j < total) {
+            const uint32_t excl = incl - cnt;
+            const bool mine = j >= excl && j < incl;
+            const int owner = __ffs(__ballot_sync(kFull, mine)) - 1;
+            int32_t color = 0;
+            if (mine) {
+                const uint32_t jj = j - excl;
+                const uint32_t p0 = __popc(w0);
+                const int bit = jj < p0 ? select_bit32(w0, jj) : 32 + select_bit32(w1, jj - p0);
+                color = base + 64 * l + bit;
+            }
+            color = __shfl_sync(kFull, color, owner);
+            __syncwarp();
+            return color;
+        }
+        j -= total;
+        base += 32 * kWarpBitmapWords;
+        __syncwarp();
+    }
+}
+
+struct BlockScratch {
+    uint32_t bm[kBlockBitmapWords];
+    uint32_t wsum[kWarps];
+    int32_t result;
+};
+
+// Block path: the whole block on one vertex, bitmap of 131072 colors per
+// window.  Every thread of the block must call it.
+template <class Fetch>
+__device__ __forceinline__ int32_t choose_block(const Graph& g, int64_t beg, int64_t end,
+                                                uint32_t j, Fetch& fetch, BlockScratch& s,
+                                                uint32_t* err) {
+    constexpr int kPer = kBlockBitmapWords / kBlock;
+    const int t = threadIdx.x, l = lane_id(), w = t >> 5;
+    int32_t base = 1;
+    for (;;) {
+        for (int i = t; i < kBlockBitmapWords; i += kBlock) s.bm[i] = 0u;
+        __syncthreads();
+        for (int64_t e = beg + t; e < end; e += kBlock) {
+            const int32_t u = load_nbr(g, e, err);
+            if (u < 0) continue;
+            const int32_t c = fetch(u);
+            const uint32_t d = static_cast<uint32_t>(c - base);
+            if (c > 0 && d < 32u * kBlockBitmapWords) atomicOr(&s.bm[d >> 5], 1u << (d & 31));
+        }
+        __syncthreads();
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) cnt += __popc(~s.bm[t * kPer + i]);
+        const uint32_t incl_w = warp_inclusive_scan(cnt);
+        if (l == 31) s.wsum[w] = incl_w;
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+#pragma unroll
+        for (int i = 0; i < kWarps; ++i) {
+            const uint32_t x = s.wsum[i];
+            if (i < w) before += x;
+            total += x;
+        }
+        const uint32_t incl = incl_w + before, excl = incl - cnt;
+        if (j < total) {
+            if (j >= excl && j < incl) {
+                uint32_t jj = j - excl;
+                for (int i = 0; i < kPer; ++i) {
+                    const uint32_t f = ~s.bm[t * kPer + i];
+                    const uint32_t pc = __popc(f);
+                    if (jj < pc) {
+                        s.result = base + 32 * (t * kPer + i) + select_bit32(f, jj);
+                        break;
+                    }
+                    jj -= pc;
+                }
+            }
+            __syncthreads();
+            const int32_t color = s.result;
+            __syncthreads();
+            return color;
+        }
+        j -= total;
+        base += 32 * kBlockBitmapWords;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tiles: a list is cut into segments (one bucket each); segment s holds
+// tiles tile_prefix[s] .. tile_prefix[s+1]-1 of bucket_tile(bucket) vertices.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_segment(const int32_t* prefix, int nseg, int32_t t) {
+    int lo = 0, hi = nseg - 1;  // largest s with prefix[s] <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Warp-aggregated append of `want` lanes into list[start + counter++].
+__device__ __forceinline__ void warp_append(bool want, int32_t v, int32_t* counter,
+                                            int32_t* list, int32_t start) {
+    const uint32_t b = __ballot_sync(kFull, want);
+    if (b == 0) return;
+    const int l = lane_id();
+    const int leader = __ffs(b) - 1;
+    int32_t base = 0;
+    if (l == leader) base = atomicAdd(counter, __popc(b));
+    base = __shfl_sync(kFull, base, leader);
+    if (want) list[start + base + __popc(b & ((1u << l) - 1u))] = v;
+}
+
+// Warp-wide sum of a per-thread count added to a global counter (one atomic
+// per warp).  The whole warp must call it.
+__device__ __forceinline__ void warp_add(unsigned long long* dst, unsigned long long x) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
+    if (lane_id() == 0 && x != 0) atomicAdd(dst, x);
+}
+
+__device__ __forceinline__ void warp_max(int32_t* dst, int32_t x) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) x = max(x, __shfl_xor_sync(kFull, x, d));
+    if (lane_id() == 0) atomicMax(dst, x);
+}
+
+}  // namespace gc

@@ -1,0 +1,88 @@
+// gc_internal.h -- host-side plumbing shared by the library's translation
+// units: the scratch pool, launch accounting, error mapping and the internal
+// (device-pointer) implementations behind the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gc.h"
+#include "gc_common.cuh"
+
+namespace gc {
+
+// Stream-ordered scratch from a library-owned memory pool (kept warm across
+// calls).  Returns nullptr on failure.
+void* scratch_alloc(size_t bytes, cudaStream_t s);
+void scratch_free(void* p, cudaStream_t s);
+
+// Number of SMs of the current device (cached).
+int sm_count();
+// Default persistent grid: blocks_per_sm resident blocks on every SM.
+int persistent_grid(const Tuning& t, int blocks_per_sm = 8);
+
+// Process-wide count of kernel launches made by the library.
+void note_launches(int64_t k);
+
+// Kernel timing (gc_profile_enable): events around each launch.
+enum KernelId {
+    KID_SPEC_SETUP, KID_SPEC_FILL, KID_TENTATIVE, KID_CONFLICT, KID_PRIORITIES,
+    KID_RC_BUCKET, KID_RC_VALIDATE, KID_RC_HIST, KID_RC_ORDER, KID_RC_SCATTER,
+    KID_RC_RECOLOR, KID_RC_STEP, KID_VALIDATE, KID_MARK_PRESENT, KID_COUNT_BITS,
+    KID_CHECK_GRAPH, KID_COUNT_
+};
+void prof_begin(KernelId k, cudaStream_t s);
+void prof_end(KernelId k, cudaStream_t s);
+// Folds the finished launches into the totals (call after a stream sync).
+void prof_collect();
+
+#define GC_LAUNCH(kid, stream, ...)              \
+    do {                                          \
+        ::gc::prof_begin((kid), (stream));        \
+        __VA_ARGS__;                              \
+        ::gc::prof_end((kid), (stream));          \
+        ::gc::note_launches(1);                   \
+    } while (0)
+
+// The tuning in force (set with gc_set_tuning).
+Tuning current_tuning();
+
+gc_status cuda_status(cudaError_t e);
+gc_status status_from_err_bits(uint32_t bits);
+
+// RAII holder for one scratch buffer.
+struct Scratch {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    Scratch() = default;
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+    ~Scratch() { if (p) scratch_free(p, s); }
+    bool alloc(size_t bytes, cudaStream_t st) {
+        s = st;
+        p = scratch_alloc(bytes ? bytes : 16, st);
+        return p != nullptr;
+    }
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Speculative coloring on device pointers; writes colors_out (device) and,
+// if given, stats.  maxc_out receives the max color (host).
+gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors_out,
+                       gc_stats* stats, cudaStream_t s);
+
+// Recoloring on device pointers.  When `trusted` the input is known proper
+// (our own gc_color output) and maxc_in is its max color; otherwise the
+// input is validated first.  colors_out may alias colors_in.
+gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_in, bool trusted,
+                         int32_t perm, int32_t iterations, uint64_t seed, int32_t* colors_out,
+                         int32_t* ncolors_per_iter, gc_stats* stats, cudaStream_t s);
+
+gc_status priorities_device(uint64_t seed, int64_t n, uint32_t* out, cudaStream_t s);
+
+gc_status validate_device(const Graph& g, const int32_t* colors, gc_validation* out,
+                          cudaStream_t s);
+
+gc_status check_graph_device(const Graph& g, int64_t* first_bad, cudaStream_t s);
+
+}  // namespace gc

@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads and exports every symbol include/gc.h
+declares (no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "gc.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(gc_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1407_6745_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_path():
+    names = _declared()
+    for must in ("gc_color", "gc_recolor", "gc_color_recolor", "gc_validate", "gc_check_graph",
+                 "gc_status_string", "gc_version"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_host_only_entry_points(lib):
+    lib.gc_status_string.restype = ctypes.c_char_p
+    assert lib.gc_status_string(0) == b"ok"
+    assert lib.gc_status_string(3) == b"input coloring is not proper"
+    assert lib.gc_version() >= 100
+
+
+def test_argument_checks_need_no_gpu():
+    """Invalid arguments are rejected on the host before any CUDA call."""
+    import torch
+    import paper_1407_6745_gb300 as gc
+    off = torch.tensor([0, 1, 2], dtype=torch.int64)
+    idx = torch.tensor([1, 0], dtype=torch.int32)
+    with pytest.raises(gc.GCError) as e:
+        gc.gc_color(off, idx, "RXF", X=0)
+    assert e.value.name == "GC_ERR_INVALID_ARG"
+    with pytest.raises(gc.GCError) as e:
+        gc.gc_recolor(off, idx, torch.ones(2, dtype=torch.int32), perm=7)
+    assert e.value.name == "GC_ERR_INVALID_ARG"
+    with pytest.raises(gc.GCError):
+        gc.gc_set_tuning(g4_max_deg=9, g8_max_deg=8)
+    gc.gc_set_tuning()
+    assert gc.gc_get_tuning()["warp_max_deg"] == 2048
