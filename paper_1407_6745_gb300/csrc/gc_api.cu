@@ -84,6 +84,21 @@ int sm_count() {
     return g_sms[dev];
 }
 
+int occupancy_of(const void* kernel, int threads) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<const void*, int>, int>> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    for (const auto& e : cache)
+        if (e.first.first == kernel && e.first.second == dev) return e.second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess || nb < 1)
+        nb = 1;
+    cache.push_back({{kernel, dev}, nb});
+    return nb;
+}
+
 int persistent_grid(const Tuning& t, int blocks_per_sm) {
     if (t.grid_blocks > 0) return t.grid_blocks;
     return sm_count() * blocks_per_sm;
@@ -98,8 +113,8 @@ namespace {
 const char* const kKernelNames[KID_COUNT_] = {
     "k_spec_setup", "k_spec_fill", "k_tentative", "k_conflict", "k_priorities",
     "k_rc_bucket", "k_rc_validate", "k_rc_hist", "k_rc_order", "k_rc_scatter",
-    "k_rc_recolor_dataflow", "k_rc_recolor_step", "k_validate", "k_mark_present",
-    "k_count_bits", "k_check_graph"};
+    "k_rc_recolor_dataflow", "k_rc_recolor_step", "k_validate", "k_validate_heavy",
+    "k_mark_present", "k_count_bits", "k_check_graph"};
 std::atomic<bool> g_prof_on{false};
 std::mutex g_prof_mu;
 long long g_prof_launches[KID_COUNT_];

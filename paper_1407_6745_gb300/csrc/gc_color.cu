@@ -43,12 +43,12 @@ struct SpecArgs {
     int32_t X;
     uint64_t seed;
     Tuning tune;
-    int32_t* color;   // fixed colors (0 = in the work set)
-    int32_t* tent;    // tentative colors
-    uint32_t* prio;   // priorities
-    uint8_t* bucket;  // degree bucket per vertex
-    int32_t* list0;
-    int32_t* list1;
+    int32_t* color;    // fixed colors (0 = in the work set)
+    int32_t* tent;     // tentative colors
+    uint32_t* prio;    // priorities
+    uint8_t* bucket;   // degree bucket per vertex
+    WorkItem* list0;   // work lists (ping-pong), bucket regions
+    WorkItem* list1;
     SpecCtrl* ctrl;
 };
 
@@ -60,10 +60,10 @@ __global__ void __launch_bounds__(kBlock) k_spec_setup(SpecArgs a) {
     int32_t my_max_deg = 0;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; i < a.g.n; i += stride) {
         const int32_t v = static_cast<int32_t>(i);
-        int64_t beg, end;
-        row_range(a.g, v, beg, end, &a.ctrl->err);
-        const int64_t deg = end - beg;
-        my_max_deg = max(my_max_deg, static_cast<int32_t>(deg < INT32_MAX ? deg : INT32_MAX));
+        int64_t beg;
+        int32_t deg;
+        row_of(a.g, v, beg, deg, &a.ctrl->err);
+        my_max_deg = max(my_max_deg, deg);
         const int b = bucket_of(deg, a.X, a.tune);
         a.bucket[v] = static_cast<uint8_t>(b);
         a.prio[v] = prio_of(a.seed, v);
@@ -94,13 +94,16 @@ __global__ void __launch_bounds__(kBlock) k_spec_fill(SpecArgs a) {
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; i < a.g.n; i += stride) {
         const int32_t v = static_cast<int32_t>(i);
         const int b = a.bucket[v];
+        int64_t beg;
+        int32_t deg;
+        row_of(a.g, v, beg, deg, &a.ctrl->err);
         const unsigned act = __activemask();
         const unsigned peers = __match_any_sync(act, b);
         const int leader = __ffs(peers) - 1;
         int32_t base = 0;
         if (lane_id() == leader) base = atomicAdd(&a.ctrl->cnt[0][b], __popc(peers));
         base = __shfl_sync(peers, base, leader);
-        a.list0[s_start[b] + base + __popc(peers & ((1u << lane_id()) - 1u))] = v;
+        store_item(a.list0 + s_start[b] + base + __popc(peers & ((1u << lane_id()) - 1u)), beg, v, deg);
     }
 }
 
@@ -136,30 +139,34 @@ union SpecShared {
     uint32_t warp_bm[kWarps][kWarpBitmapWords];
 };
 
+// Colors fixed before the round (the snapshot); 0 = in the work set.
+struct SnapshotFetch {
+    const int32_t* color;
+    __device__ __forceinline__ int32_t raw(int32_t u) const { return __ldg(color + u); }
+    __device__ __forceinline__ int32_t resolve(int32_t, int32_t x) const { return x; }
+};
+
 // ---------------------------------------------------------------------------
 // Tentative coloring of W_r against the snapshot `color`
 // ---------------------------------------------------------------------------
 template <int G, bool kRXF>
 __device__ __forceinline__ void tentative_group_tile(const SpecArgs& a, const RoundTiles& rt,
-                                                     const int32_t* list, int b, int32_t first,
+                                                     const WorkItem* list, int b, int32_t first,
                                                      int32_t round, unsigned long long& edges) {
     const int gi = threadIdx.x / G, gl = threadIdx.x % G;
     const int32_t k = first + gi;
     const bool valid = k < rt.cnt[b];
-    int32_t v = 0;
-    int64_t beg = 0, end = 0;
+    WorkItem it{0, 0, 0};
     uint32_t j = 0;
     if (valid) {
-        v = list[rt.start[b] + k];
-        row_range(a.g, v, beg, end, &a.ctrl->err);
-        if (kRXF) j = scale_index(rxf_word(a.seed, v, round), static_cast<uint32_t>(a.X));
+        it = load_item(list + rt.start[b] + k);
+        if (kRXF) j = scale_index(rxf_word(a.seed, it.v, round), static_cast<uint32_t>(a.X));
     }
-    const int32_t* color = a.color;
-    auto fetch = [color](int32_t u) { return __ldg(color + u); };
-    const int32_t c = choose_reg<G>(a.g, beg, end, gl, j, fetch, &a.ctrl->err);
+    const SnapshotFetch fetch{a.color};
+    const int32_t c = choose_reg<G, LanesUnroll<G>::U>(a.g, it.beg, it.deg, gl, j, fetch, &a.ctrl->err);
     if (valid && gl == 0) {
-        a.tent[v] = c;
-        edges += static_cast<unsigned long long>(end - beg);
+        a.tent[it.v] = c;
+        edges += static_cast<unsigned long long>(it.deg);
     }
 }
 
@@ -169,25 +176,22 @@ __global__ void __launch_bounds__(kBlock) k_tentative(SpecArgs a) {
     __shared__ RoundTiles rt;
     const int32_t round = a.ctrl->round;
     const int par = round & 1;
-    const int32_t* list = par ? a.list1 : a.list0;
+    const WorkItem* list = par ? a.list1 : a.list0;
     if (blockIdx.x == 0 && threadIdx.x < kNB) a.ctrl->cnt[par ^ 1][threadIdx.x] = 0;
     load_round_tiles(a.ctrl, par, rt);
     unsigned long long edges = 0;
-    const int32_t* color = a.color;
-    auto fetch = [color](int32_t u) { return __ldg(color + u); };
+    const SnapshotFetch fetch{a.color};
     for (int32_t t = blockIdx.x; t < rt.prefix[kNB]; t += gridDim.x) {
         const int b = tile_bucket(rt, t);
         const int32_t first = (t - rt.prefix[b]) * bucket_tile(b);
         switch (b) {
         case 0: {
-            const int32_t v = list[rt.start[0] + first];
-            int64_t beg, end;
-            row_range(a.g, v, beg, end, &a.ctrl->err);
-            const uint32_t j = kRXF ? scale_index(rxf_word(a.seed, v, round), a.X) : 0u;
-            const int32_t c = choose_block(a.g, beg, end, j, fetch, sm.blk, &a.ctrl->err);
+            const WorkItem it = load_item(list + rt.start[0] + first);
+            const uint32_t j = kRXF ? scale_index(rxf_word(a.seed, it.v, round), a.X) : 0u;
+            const int32_t c = choose_block<4>(a.g, it.beg, it.deg, j, fetch, sm.blk, &a.ctrl->err);
             if (threadIdx.x == 0) {
-                a.tent[v] = c;
-                edges += static_cast<unsigned long long>(end - beg);
+                a.tent[it.v] = c;
+                edges += static_cast<unsigned long long>(it.deg);
             }
             break;
         }
@@ -195,14 +199,12 @@ __global__ void __launch_bounds__(kBlock) k_tentative(SpecArgs a) {
             const int w = threadIdx.x >> 5;
             const int32_t k = first + w;
             if (k < rt.cnt[1]) {
-                const int32_t v = list[rt.start[1] + k];
-                int64_t beg, end;
-                row_range(a.g, v, beg, end, &a.ctrl->err);
-                const uint32_t j = kRXF ? scale_index(rxf_word(a.seed, v, round), a.X) : 0u;
-                const int32_t c = choose_warp(a.g, beg, end, j, fetch, sm.warp_bm[w], &a.ctrl->err);
+                const WorkItem it = load_item(list + rt.start[1] + k);
+                const uint32_t j = kRXF ? scale_index(rxf_word(a.seed, it.v, round), a.X) : 0u;
+                const int32_t c = choose_warp<4>(a.g, it.beg, it.deg, j, fetch, sm.warp_bm[w], &a.ctrl->err);
                 if (lane_id() == 0) {
-                    a.tent[v] = c;
-                    edges += static_cast<unsigned long long>(end - beg);
+                    a.tent[it.v] = c;
+                    edges += static_cast<unsigned long long>(it.deg);
                 }
             }
             break;
@@ -224,47 +226,54 @@ __device__ __forceinline__ bool beats(uint32_t pu, int32_t u, uint32_t pv, int32
     return pu > pv || (pu == pv && u > v);
 }
 
-template <int G>
-__device__ __forceinline__ bool loses(const SpecArgs& a, int32_t v, int64_t beg, int64_t end,
-                                      int gl) {
-    bool lose = false;
-    if (end > beg) {
-        const int32_t tv = __ldg(a.tent + v);
-        const uint32_t pv = __ldg(a.prio + v);
-        for (int64_t e = beg + gl; e < end && !lose; e += G) {
-            const int32_t u = load_nbr(a.g, e, &a.ctrl->err);
-            if (u < 0 || u == v) continue;
-            if (__ldg(a.tent + u) == tv && beats(__ldg(a.prio + u), u, pv, v)) lose = true;
+// Does some neighbor in this lane's stripe have v's tentative color and a
+// larger (priority, id)?  U neighbor loads in flight per lane.
+template <int U>
+__device__ __forceinline__ bool loses(const SpecArgs& a, const WorkItem& it, int32_t lane0,
+                                      int32_t stride) {
+    if (it.deg == 0) return false;
+    const int32_t tv = __ldg(a.tent + it.v);
+    const uint32_t pv = __ldg(a.prio + it.v);
+    for (int32_t k0 = lane0; k0 < it.deg; k0 += stride * U) {
+        int32_t u[U], t[U];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const int32_t k = k0 + i * stride;
+            u[i] = k < it.deg ? load_nbr(a.g, it.beg + k, &a.ctrl->err) : -1;
         }
+#pragma unroll
+        for (int i = 0; i < U; ++i) t[i] = __ldg(a.tent + (u[i] >= 0 ? u[i] : 0));
+        bool lose = false;
+#pragma unroll
+        for (int i = 0; i < U; ++i)
+            if (u[i] >= 0 && u[i] != it.v && t[i] == tv && beats(__ldg(a.prio + u[i]), u[i], pv, it.v))
+                lose = true;
+        if (lose) return true;
     }
-    return lose;
+    return false;
 }
 
 template <int G>
 __device__ __forceinline__ void conflict_group_tile(const SpecArgs& a, const RoundTiles& rt,
-                                                    const int32_t* list, int32_t* next, int par,
+                                                    const WorkItem* list, WorkItem* next, int par,
                                                     int b, int32_t first, int32_t& my_max,
                                                     unsigned long long& edges) {
     const int gi = threadIdx.x / G, gl = threadIdx.x % G;
     const int32_t k = first + gi;
     const bool valid = k < rt.cnt[b];
-    int32_t v = 0;
-    int64_t beg = 0, end = 0;
-    if (valid) {
-        v = list[rt.start[b] + k];
-        row_range(a.g, v, beg, end, &a.ctrl->err);
-    }
-    const bool lose = group_any<G>(loses<G>(a, v, beg, end, gl));
+    WorkItem it{0, 0, 0};
+    if (valid) it = load_item(list + rt.start[b] + k);
+    const bool lose = group_any<G>(loses<LanesUnroll<G>::U>(a, it, gl, G));
     const bool leader = valid && gl == 0;
     if (leader) {
-        edges += static_cast<unsigned long long>(end - beg);
+        edges += static_cast<unsigned long long>(it.deg);
         if (!lose) {
-            const int32_t c = __ldg(a.tent + v);
-            a.color[v] = c;
+            const int32_t c = __ldg(a.tent + it.v);
+            a.color[it.v] = c;
             my_max = max(my_max, c);
         }
     }
-    warp_append(leader && lose, v, &a.ctrl->cnt[par ^ 1][b], next, rt.start[b]);
+    warp_append(leader && lose, it.beg, it.v, it.deg, &a.ctrl->cnt[par ^ 1][b], next, rt.start[b]);
 }
 
 __global__ void __launch_bounds__(kBlock) k_conflict(SpecArgs a) {
@@ -272,8 +281,8 @@ __global__ void __launch_bounds__(kBlock) k_conflict(SpecArgs a) {
     __shared__ bool s_last;
     const int32_t round = a.ctrl->round;
     const int par = round & 1;
-    const int32_t* list = par ? a.list1 : a.list0;
-    int32_t* next = par ? a.list0 : a.list1;
+    const WorkItem* list = par ? a.list1 : a.list0;
+    WorkItem* next = par ? a.list0 : a.list1;
     load_round_tiles(a.ctrl, par, rt);
     unsigned long long edges = 0;
     int32_t my_max = 0;
@@ -282,18 +291,16 @@ __global__ void __launch_bounds__(kBlock) k_conflict(SpecArgs a) {
         const int32_t first = (t - rt.prefix[b]) * bucket_tile(b);
         switch (b) {
         case 0: {
-            const int32_t v = list[rt.start[0] + first];
-            int64_t beg, end;
-            row_range(a.g, v, beg, end, &a.ctrl->err);
-            const bool lose = __syncthreads_or(loses<kBlock>(a, v, beg, end, threadIdx.x));
+            const WorkItem it = load_item(list + rt.start[0] + first);
+            const bool lose = __syncthreads_or(loses<4>(a, it, threadIdx.x, kBlock));
             if (threadIdx.x == 0) {
-                edges += static_cast<unsigned long long>(end - beg);
+                edges += static_cast<unsigned long long>(it.deg);
                 if (lose) {
                     const int32_t pos = atomicAdd(&a.ctrl->cnt[par ^ 1][0], 1);
-                    next[rt.start[0] + pos] = v;
+                    store_item(next + rt.start[0] + pos, it.beg, it.v, it.deg);
                 } else {
-                    const int32_t c = a.tent[v];
-                    a.color[v] = c;
+                    const int32_t c = a.tent[it.v];
+                    a.color[it.v] = c;
                     my_max = max(my_max, c);
                 }
             }
@@ -360,8 +367,9 @@ gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors
     if (!t_pinned.p) return GC_ERR_OOM;
     const int64_t n = g.n;
     Scratch sc_tent, sc_prio, sc_l0, sc_l1, sc_bucket, sc_ctrl;
-    if (!sc_tent.alloc(n * 4, s) || !sc_prio.alloc(n * 4, s) || !sc_l0.alloc(n * 4, s) ||
-        !sc_l1.alloc(n * 4, s) || !sc_bucket.alloc(n, s) || !sc_ctrl.alloc(sizeof(SpecCtrl), s))
+    if (!sc_tent.alloc(n * 4, s) || !sc_prio.alloc(n * 4, s) ||
+        !sc_l0.alloc(n * sizeof(WorkItem), s) || !sc_l1.alloc(n * sizeof(WorkItem), s) ||
+        !sc_bucket.alloc(n, s) || !sc_ctrl.alloc(sizeof(SpecCtrl), s))
         return GC_ERR_OOM;
     SpecArgs a;
     a.g = g;
@@ -372,8 +380,8 @@ gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors
     a.tent = sc_tent.as<int32_t>();
     a.prio = sc_prio.as<uint32_t>();
     a.bucket = sc_bucket.as<uint8_t>();
-    a.list0 = sc_l0.as<int32_t>();
-    a.list1 = sc_l1.as<int32_t>();
+    a.list0 = sc_l0.as<WorkItem>();
+    a.list1 = sc_l1.as<WorkItem>();
     a.ctrl = sc_ctrl.as<SpecCtrl>();
 
     cudaEvent_t e0, e1;
@@ -381,16 +389,18 @@ gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
     cudaMemsetAsync(a.ctrl, 0, sizeof(SpecCtrl), s);
-    const int grid = persistent_grid(a.tune);
-    const int setup_grid = static_cast<int>(std::min<int64_t>((n + kBlock - 1) / kBlock, grid));
+    const int grid_t = resident_grid(X > 1 ? k_tentative<true> : k_tentative<false>, a.tune);
+    const int grid_c = resident_grid(k_conflict, a.tune);
+    const int setup_grid = static_cast<int>(
+        std::min<int64_t>((n + kBlock - 1) / kBlock, resident_grid(k_spec_setup, a.tune)));
     GC_LAUNCH(KID_SPEC_SETUP, s, k_spec_setup<<<setup_grid, kBlock, 0, s>>>(a));
     GC_LAUNCH(KID_SPEC_FILL, s, k_spec_fill<<<setup_grid, kBlock, 0, s>>>(a));
     gc_status st = GC_OK;
     int32_t rounds = 0;
     for (;;) {
-        if (X > 1) GC_LAUNCH(KID_TENTATIVE, s, k_tentative<true><<<grid, kBlock, 0, s>>>(a));
-        else GC_LAUNCH(KID_TENTATIVE, s, k_tentative<false><<<grid, kBlock, 0, s>>>(a));
-        GC_LAUNCH(KID_CONFLICT, s, k_conflict<<<grid, kBlock, 0, s>>>(a));
+        if (X > 1) GC_LAUNCH(KID_TENTATIVE, s, k_tentative<true><<<grid_t, kBlock, 0, s>>>(a));
+        else GC_LAUNCH(KID_TENTATIVE, s, k_tentative<false><<<grid_t, kBlock, 0, s>>>(a));
+        GC_LAUNCH(KID_CONFLICT, s, k_conflict<<<grid_c, kBlock, 0, s>>>(a));
         ++rounds;
         cudaMemcpyAsync(t_pinned.p, &a.ctrl->active, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         cudaError_t ce = cudaStreamSynchronize(s);

@@ -192,22 +192,85 @@ __device__ __forceinline__ int32_t load_nbr(const Graph& g, int64_t e, uint32_t*
 }
 
 // ---------------------------------------------------------------------------
-// Color choice: the j-th (0-based) color >= 1 not returned by fetch(u) for a
-// neighbor u.  fetch returns the neighbor's color, or a value < 1 to ignore it.
+// Work items: a vertex with its adjacency row, so a kernel reaches the row
+// without a dependent load of the offsets.  16 bytes, one vector load.
 // ---------------------------------------------------------------------------
+struct __align__(16) WorkItem {
+    int64_t beg;
+    int32_t v;
+    int32_t deg;
+};
+
+__device__ __forceinline__ WorkItem load_item(const WorkItem* p) {
+    const int4 r = __ldcg(reinterpret_cast<const int4*>(p));
+    WorkItem w;
+    w.beg = (static_cast<int64_t>(static_cast<uint32_t>(r.y)) << 32) | static_cast<uint32_t>(r.x);
+    w.v = r.z;
+    w.deg = r.w;
+    return w;
+}
+
+__device__ __forceinline__ void store_item(WorkItem* p, int64_t beg, int32_t v, int32_t deg) {
+    int4 r;
+    r.x = static_cast<int32_t>(static_cast<uint64_t>(beg));
+    r.y = static_cast<int32_t>(static_cast<uint64_t>(beg) >> 32);
+    r.z = v;
+    r.w = deg;
+    *reinterpret_cast<int4*>(p) = r;
+}
+
+// Row of v as (beg, deg) with the checks that keep every later load in
+// bounds: a malformed row is flagged and treated as empty.
+__device__ __forceinline__ void row_of(const Graph& g, int32_t v, int64_t& beg, int32_t& deg,
+                                       uint32_t* err) {
+    int64_t b = __ldg(g.off + v), e = __ldg(g.off + v + 1);
+    if (b < 0 || e < b || e > g.nnz || e - b > INT32_MAX) {
+        atomicOr(err, kErrBadGraph);
+        b = e = 0;
+    }
+    beg = b;
+    deg = static_cast<int32_t>(e - b);
+}
+
+// ---------------------------------------------------------------------------
+// Color choice: the j-th (0-based) color >= 1 not used by a neighbor.
+//
+// A Fetch gives a neighbor's color in two steps: raw(u) issues the load (no
+// branch, so a batch of U loads is in flight at once) and resolve(u, x)
+// turns the loaded word into a color, or a value < 1 to ignore the neighbor.
+// Each lane takes the neighbors lane0, lane0 + stride, ...; U per batch.
+// ---------------------------------------------------------------------------
+template <int U, class Fetch, class Mark>
+__device__ __forceinline__ void scan_row(const Graph& g, int64_t beg, int32_t deg, int32_t lane0,
+                                         int32_t stride, const Fetch& fetch, Mark&& mark,
+                                         uint32_t* err) {
+    for (int32_t k0 = lane0; k0 < deg; k0 += stride * U) {
+        int32_t u[U];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const int32_t k = k0 + i * stride;
+            u[i] = k < deg ? load_nbr(g, beg + k, err) : -1;
+        }
+        int32_t x[U];
+#pragma unroll
+        for (int i = 0; i < U; ++i) x[i] = fetch.raw(u[i] >= 0 ? u[i] : 0);
+#pragma unroll
+        for (int i = 0; i < U; ++i)
+            if (u[i] >= 0) mark(fetch.resolve(u[i], x[i]));
+    }
+}
 
 // Register path, G lanes per vertex; requires deg + j < 64.  All 32 lanes of
-// the warp must call it (lanes without a vertex pass an empty range).
-template <int G, class Fetch>
-__device__ __forceinline__ int32_t choose_reg(const Graph& g, int64_t beg, int64_t end, int gl,
-                                              uint32_t j, Fetch& fetch, uint32_t* err) {
+// the warp must call it (lanes without a vertex pass deg = 0).
+template <int G, int U, class Fetch>
+__device__ __forceinline__ int32_t choose_reg(const Graph& g, int64_t beg, int32_t deg, int gl,
+                                              uint32_t j, const Fetch& fetch, uint32_t* err) {
     uint64_t m = 0;
-    for (int64_t e = beg + gl; e < end; e += G) {
-        const int32_t u = load_nbr(g, e, err);
-        if (u < 0) continue;
-        const int32_t c = fetch(u);
-        if (static_cast<uint32_t>(c - 1) < 64u) m |= 1ull << (c - 1);
-    }
+    scan_row<U>(g, beg, deg, gl, G, fetch,
+                [&](int32_t c) {
+                    if (static_cast<uint32_t>(c - 1) < 64u) m |= 1ull << (c - 1);
+                },
+                err);
     m = group_or<G>(m);
     const uint64_t free_bits = ~m;
     if (j == 0) return __ffsll(static_cast<long long>(free_bits));
@@ -216,9 +279,9 @@ __device__ __forceinline__ int32_t choose_reg(const Graph& g, int64_t beg, int64
 
 // Warp path with a 64-word shared bitmap (2048 colors per window); windows
 // advance until the j-th permissible color is found.  Whole warp, one vertex.
-template <class Fetch>
-__device__ __forceinline__ int32_t choose_warp(const Graph& g, int64_t beg, int64_t end,
-                                               uint32_t j, Fetch& fetch, uint32_t* bm,
+template <int U, class Fetch>
+__device__ __forceinline__ int32_t choose_warp(const Graph& g, int64_t beg, int32_t deg,
+                                               uint32_t j, const Fetch& fetch, uint32_t* bm,
                                                uint32_t* err) {
     const int l = lane_id();
     int32_t base = 1;
@@ -226,13 +289,12 @@ __device__ __forceinline__ int32_t choose_warp(const Graph& g, int64_t beg, int6
         bm[l] = 0u;
         bm[l + 32] = 0u;
         __syncwarp();
-        for (int64_t e = beg + l; e < end; e += 32) {
-            const int32_t u = load_nbr(g, e, err);
-            if (u < 0) continue;
-            const int32_t c = fetch(u);
-            const uint32_t d = static_cast<uint32_t>(c - base);
-            if (c > 0 && d < 32u * kWarpBitmapWords) atomicOr(&bm[d >> 5], 1u << (d & 31));
-        }
+        scan_row<U>(g, beg, deg, l, 32, fetch,
+                    [&](int32_t c) {
+                        const uint32_t d = static_cast<uint32_t>(c - base);
+                        if (c > 0 && d < 32u * kWarpBitmapWords) atomicOr(&bm[d >> 5], 1u << (d & 31));
+                    },
+                    err);
         __syncwarp();
         const uint32_t w0 = ~bm[2 * l], w1 = ~bm[2 * l + 1];
         const uint32_t cnt = __popc(w0) + __popc(w1);
@@ -267,9 +329,9 @@ struct BlockScratch {
 
 // Block path: the whole block on one vertex, bitmap of 131072 colors per
 // window.  Every thread of the block must call it.
-template <class Fetch>
-__device__ __forceinline__ int32_t choose_block(const Graph& g, int64_t beg, int64_t end,
-                                                uint32_t j, Fetch& fetch, BlockScratch& s,
+template <int U, class Fetch>
+__device__ __forceinline__ int32_t choose_block(const Graph& g, int64_t beg, int32_t deg,
+                                                uint32_t j, const Fetch& fetch, BlockScratch& s,
                                                 uint32_t* err) {
     constexpr int kPer = kBlockBitmapWords / kBlock;
     const int t = threadIdx.x, l = lane_id(), w = t >> 5;
@@ -277,13 +339,12 @@ __device__ __forceinline__ int32_t choose_block(const Graph& g, int64_t beg, int
     for (;;) {
         for (int i = t; i < kBlockBitmapWords; i += kBlock) s.bm[i] = 0u;
         __syncthreads();
-        for (int64_t e = beg + t; e < end; e += kBlock) {
-            const int32_t u = load_nbr(g, e, err);
-            if (u < 0) continue;
-            const int32_t c = fetch(u);
-            const uint32_t d = static_cast<uint32_t>(c - base);
-            if (c > 0 && d < 32u * kBlockBitmapWords) atomicOr(&s.bm[d >> 5], 1u << (d & 31));
-        }
+        scan_row<U>(g, beg, deg, t, kBlock, fetch,
+                    [&](int32_t c) {
+                        const uint32_t d = static_cast<uint32_t>(c - base);
+                        if (c > 0 && d < 32u * kBlockBitmapWords) atomicOr(&s.bm[d >> 5], 1u << (d & 31));
+                    },
+                    err);
         __syncthreads();
         uint32_t cnt = 0;
 #pragma unroll
@@ -323,6 +384,9 @@ __device__ __forceinline__ int32_t choose_block(const Graph& g, int64_t beg, int
     }
 }
 
+// Neighbor-loads per lane in flight, per bucket (group of 32/16/8/4 lanes).
+template <int G> struct LanesUnroll { static constexpr int U = G == 32 ? 2 : G == 16 ? 4 : 8; };
+
 // ---------------------------------------------------------------------------
 // Tiles: a list is cut into segments (one bucket each); segment s holds
 // tiles tile_prefix[s] .. tile_prefix[s+1]-1 of bucket_tile(bucket) vertices.
@@ -336,9 +400,10 @@ __device__ __forceinline__ int find_segment(const int32_t* prefix, int nseg, int
     return lo;
 }
 
-// Warp-aggregated append of `want` lanes into list[start + counter++].
-__device__ __forceinline__ void warp_append(bool want, int32_t v, int32_t* counter,
-                                            int32_t* list, int32_t start) {
+// Warp-aggregated append of the items of the lanes with `want` into
+// list[start + counter++].  The whole warp must call it.
+__device__ __forceinline__ void warp_append(bool want, int64_t beg, int32_t v, int32_t deg,
+                                            int32_t* counter, WorkItem* list, int32_t start) {
     const uint32_t b = __ballot_sync(kFull, want);
     if (b == 0) return;
     const int l = lane_id();
@@ -346,7 +411,7 @@ __device__ __forceinline__ void warp_append(bool want, int32_t v, int32_t* count
     int32_t base = 0;
     if (l == leader) base = atomicAdd(counter, __popc(b));
     base = __shfl_sync(kFull, base, leader);
-    if (want) list[start + base + __popc(b & ((1u << l) - 1u))] = v;
+    if (want) store_item(list + start + base + __popc(b & ((1u << l) - 1u)), beg, v, deg);
 }
 
 // Warp-wide sum of a per-thread count added to a global counter (one atomic

@@ -21,6 +21,17 @@ int sm_count();
 // Default persistent grid: blocks_per_sm resident blocks on every SM.
 int persistent_grid(const Tuning& t, int blocks_per_sm = 8);
 
+// Resident blocks per SM of a kernel at kBlock threads (cached per kernel).
+int occupancy_of(const void* kernel, int threads);
+
+// Grid of a persistent (grid-stride) kernel: every block resident at once,
+// unless the tuning fixes the grid size.
+template <class K>
+int resident_grid(K kernel, const Tuning& t, int threads = kBlock) {
+    if (t.grid_blocks > 0) return t.grid_blocks;
+    return sm_count() * occupancy_of(reinterpret_cast<const void*>(kernel), threads);
+}
+
 // Process-wide count of kernel launches made by the library.
 void note_launches(int64_t k);
 
@@ -28,8 +39,8 @@ void note_launches(int64_t k);
 enum KernelId {
     KID_SPEC_SETUP, KID_SPEC_FILL, KID_TENTATIVE, KID_CONFLICT, KID_PRIORITIES,
     KID_RC_BUCKET, KID_RC_VALIDATE, KID_RC_HIST, KID_RC_ORDER, KID_RC_SCATTER,
-    KID_RC_RECOLOR, KID_RC_STEP, KID_VALIDATE, KID_MARK_PRESENT, KID_COUNT_BITS,
-    KID_CHECK_GRAPH, KID_COUNT_
+    KID_RC_RECOLOR, KID_RC_STEP, KID_VALIDATE, KID_VALIDATE_HEAVY, KID_MARK_PRESENT,
+    KID_COUNT_BITS, KID_CHECK_GRAPH, KID_COUNT_
 };
 void prof_begin(KernelId k, cudaStream_t s);
 void prof_end(KernelId k, cudaStream_t s);

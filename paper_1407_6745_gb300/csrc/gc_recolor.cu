@@ -66,14 +66,14 @@ struct RcArgs {
     int32_t* seg_start;   // (cap + 1) * kNB + 1
     int32_t* tile_prefix; // (cap + 1) * kNB + 1
     int32_t* fill;        // (cap + 1) * kNB
-    int32_t* list;        // n, vertices in class-major order
+    WorkItem* list;       // n, vertices in class-major order
     int32_t* ncolors;     // iterations + 1
     RcCtrl* ctrl;
 };
 
 __device__ __forceinline__ int32_t ld_relaxed(const int32_t* p) {
     int32_t x;
-    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(x) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(x) : "l"(p));
     return x;
 }
 __device__ __forceinline__ void st_relaxed(int32_t* p, int32_t x) {
@@ -274,43 +274,94 @@ __global__ void __launch_bounds__(kOrderThreads) k_rc_order(RcArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Counting-sort scatter into class-major segments
+// Counting-sort scatter into class-major segments.  Each block takes a
+// contiguous slice of vertices, counts its vertices per segment in shared
+// memory, reserves its ranges with one global atomic per (block, segment),
+// then places the vertices.  (Order inside a segment is free: a class is an
+// independent set.)
 // ---------------------------------------------------------------------------
+constexpr int kScatterSegs = 4096;
+
+__device__ __forceinline__ int32_t segment_of(const RcArgs& a, int32_t v) {
+    return a.rank_of[a.old_c[v]] * kNB + a.bucket[v];
+}
+
+__device__ __forceinline__ void place(const RcArgs& a, int32_t v, int32_t sg, int32_t pos) {
+    int64_t beg;
+    int32_t deg;
+    row_of(a.g, v, beg, deg, &a.ctrl->err);
+    store_item(a.list + pos, beg, v, deg);
+    a.new_c[v] = -(sg / kNB + 1);
+}
+
 __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
+    __shared__ int32_t s_cnt[kScatterSegs];
+    __shared__ int32_t s_base[kScatterSegs];
     if (a.ctrl->err & (kErrImproper | kErrBadGraph)) return;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * kBlock;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; i < a.g.n; i += stride) {
+    const int32_t nseg = a.ctrl->k * kNB;
+    const int64_t chunk = (a.g.n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = blockIdx.x * chunk;
+    const int64_t hi = a.g.n < lo + chunk ? a.g.n : lo + chunk;
+    if (nseg > kScatterSegs) {
+        // many classes: warp-aggregated global atomics
+        for (int64_t i = lo + threadIdx.x; i < hi; i += kBlock) {
+            const int32_t v = static_cast<int32_t>(i);
+            const int32_t sg = segment_of(a, v);
+            const unsigned act = __activemask();
+            const unsigned peers = __match_any_sync(act, sg);
+            const int leader = __ffs(peers) - 1;
+            int32_t base = 0;
+            if (lane_id() == leader) base = atomicAdd(&a.fill[sg], __popc(peers));
+            base = __shfl_sync(peers, base, leader);
+            place(a, v, sg, a.seg_start[sg] + base + __popc(peers & ((1u << lane_id()) - 1u)));
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < nseg; i += kBlock) s_cnt[i] = 0;
+    __syncthreads();
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kBlock) {
+        const int32_t sg = segment_of(a, static_cast<int32_t>(i));
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, sg);
+        if (lane_id() == __ffs(peers) - 1) atomicAdd(&s_cnt[sg], __popc(peers));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nseg; i += kBlock) {
+        const int32_t c = s_cnt[i];
+        if (c) s_base[i] = a.seg_start[i] + atomicAdd(&a.fill[i], c);
+        s_cnt[i] = 0;
+    }
+    __syncthreads();
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kBlock) {
         const int32_t v = static_cast<int32_t>(i);
-        const int32_t c = a.old_c[v];
-        if (c < 1 || c > a.cap) continue;  // flagged by k_rc_hist
-        const int32_t p = a.rank_of[c];
-        const int32_t sg = p * kNB + a.bucket[v];
+        const int32_t sg = segment_of(a, v);
         const unsigned act = __activemask();
         const unsigned peers = __match_any_sync(act, sg);
         const int leader = __ffs(peers) - 1;
         int32_t base = 0;
-        if (lane_id() == leader) base = atomicAdd(&a.fill[sg], __popc(peers));
+        if (lane_id() == leader) base = atomicAdd(&s_cnt[sg], __popc(peers));
         base = __shfl_sync(peers, base, leader);
-        a.list[a.seg_start[sg] + base + __popc(peers & ((1u << lane_id()) - 1u))] = v;
-        a.new_c[v] = -(p + 1);
+        place(a, v, sg, s_base[sg] + base + __popc(peers & ((1u << lane_id()) - 1u)));
     }
 }
 
 // ---------------------------------------------------------------------------
 // The class steps
 // ---------------------------------------------------------------------------
-// Color of neighbor u as seen by a vertex of class rank p (0 = ignore).
+// Color of neighbor u as seen by a vertex of class rank p (< 1 = ignore).
 template <bool kDataflow>
 struct RecolorFetch {
     int32_t* new_c;
     int32_t p;
     int32_t spin_limit;
     uint32_t* err;
-    __device__ __forceinline__ int32_t operator()(int32_t u) const {
-        int32_t x = kDataflow ? ld_relaxed(new_c + u) : __ldcg(new_c + u);
+    __device__ __forceinline__ int32_t raw(int32_t u) const {
+        return kDataflow ? ld_relaxed(new_c + u) : __ldcg(new_c + u);
+    }
+    __device__ __forceinline__ int32_t resolve(int32_t u, int32_t x) const {
         if (x > 0) return x;
         if (!kDataflow || -x - 1 >= p) return 0;  // later class: not recolored yet
-        // earlier class, still in flight: bounded wait.  Once any wait of the
+        // Earlier class, still in flight: bounded wait.  Once any wait of the
         // launch has run out, every other wait gives up at once, so a launch
         // never spends more than about one spin_limit in waits.
         unsigned ns = 32;
@@ -340,75 +391,82 @@ __device__ __forceinline__ void recolor_group_tile(const RcArgs& a, const Recolo
     const int gi = threadIdx.x / G, gl = threadIdx.x % G;
     const int32_t k = first + gi;
     const bool valid = k < last;
-    int32_t v = 0;
-    int64_t beg = 0, end = 0;
-    if (valid) {
-        v = a.list[k];
-        row_range(a.g, v, beg, end, &a.ctrl->err);
-    }
-    RecolorFetch<kDataflow> fetch = f;
-    const int32_t c = choose_reg<G>(a.g, beg, end, gl, 0u, fetch, &a.ctrl->err);
+    WorkItem it{0, 0, 0};
+    if (valid) it = load_item(a.list + k);
+    const int32_t c = choose_reg<G, LanesUnroll<G>::U>(a.g, it.beg, it.deg, gl, 0u, f, &a.ctrl->err);
     if (valid && gl == 0) {
-        st_relaxed(a.new_c + v, c);
+        st_relaxed(a.new_c + it.v, c);
         my_max = max(my_max, c);
-        edges += static_cast<unsigned long long>(end - beg);
+        edges += static_cast<unsigned long long>(it.deg);
     }
 }
 
 template <bool kDataflow>
-__device__ __forceinline__ void recolor_tile(const RcArgs& a, RcShared& sm, int32_t sg, int32_t t,
+__device__ __forceinline__ void recolor_tile(const RcArgs& a, RcShared& sm, int32_t sg,
+                                             int32_t seg_first, int32_t seg_last, int32_t tile_in_seg,
                                              int32_t& my_max, unsigned long long& edges) {
     const int32_t p = sg / kNB;
     const int b = sg % kNB;
-    const int32_t first = a.seg_start[sg] + (t - a.tile_prefix[sg]) * bucket_tile(b);
-    const int32_t last = a.seg_start[sg + 1];
+    const int32_t first = seg_first + tile_in_seg * bucket_tile(b);
     const RecolorFetch<kDataflow> f{a.new_c, p, a.tune.spin_limit, &a.ctrl->err};
     switch (b) {
     case 0: {
-        const int32_t v = a.list[first];
-        int64_t beg, end;
-        row_range(a.g, v, beg, end, &a.ctrl->err);
-        RecolorFetch<kDataflow> fetch = f;
-        const int32_t c = choose_block(a.g, beg, end, 0u, fetch, sm.blk, &a.ctrl->err);
+        const WorkItem it = load_item(a.list + first);
+        const int32_t c = choose_block<4>(a.g, it.beg, it.deg, 0u, f, sm.blk, &a.ctrl->err);
         if (threadIdx.x == 0) {
-            st_relaxed(a.new_c + v, c);
+            st_relaxed(a.new_c + it.v, c);
             my_max = max(my_max, c);
-            edges += static_cast<unsigned long long>(end - beg);
+            edges += static_cast<unsigned long long>(it.deg);
         }
         break;
     }
     case 1: {
         const int w = threadIdx.x >> 5;
         const int32_t k = first + w;
-        if (k < last) {
-            const int32_t v = a.list[k];
-            int64_t beg, end;
-            row_range(a.g, v, beg, end, &a.ctrl->err);
-            RecolorFetch<kDataflow> fetch = f;
-            const int32_t c = choose_warp(a.g, beg, end, 0u, fetch, sm.warp_bm[w], &a.ctrl->err);
+        if (k < seg_last) {
+            const WorkItem it = load_item(a.list + k);
+            const int32_t c = choose_warp<4>(a.g, it.beg, it.deg, 0u, f, sm.warp_bm[w], &a.ctrl->err);
             if (lane_id() == 0) {
-                st_relaxed(a.new_c + v, c);
+                st_relaxed(a.new_c + it.v, c);
                 my_max = max(my_max, c);
-                edges += static_cast<unsigned long long>(end - beg);
+                edges += static_cast<unsigned long long>(it.deg);
             }
         }
         break;
     }
-    case 2: recolor_group_tile<32, kDataflow>(a, f, first, last, my_max, edges); break;
-    case 3: recolor_group_tile<16, kDataflow>(a, f, first, last, my_max, edges); break;
-    case 4: recolor_group_tile<8, kDataflow>(a, f, first, last, my_max, edges); break;
-    default: recolor_group_tile<4, kDataflow>(a, f, first, last, my_max, edges); break;
+    case 2: recolor_group_tile<32, kDataflow>(a, f, first, seg_last, my_max, edges); break;
+    case 3: recolor_group_tile<16, kDataflow>(a, f, first, seg_last, my_max, edges); break;
+    case 4: recolor_group_tile<8, kDataflow>(a, f, first, seg_last, my_max, edges); break;
+    default: recolor_group_tile<4, kDataflow>(a, f, first, seg_last, my_max, edges); break;
     }
 }
+
+// Segment lookup: the segment table is staged in shared memory when it fits.
+constexpr int kSegSmem = 2048;
+
+struct SegTable {
+    int32_t tile_prefix[kSegSmem + 1];
+    int32_t seg_start[kSegSmem + 1];
+};
 
 // Dataflow form: tiles claimed in class order; the next claim is taken while
 // the current tile is processed.
 __global__ void __launch_bounds__(kBlock) k_rc_recolor_dataflow(RcArgs a) {
     __shared__ RcShared sm;
+    __shared__ SegTable st;
     __shared__ int32_t s_tile, s_seg;
     if (a.ctrl->err & (kErrImproper | kErrBadGraph)) return;
     const int32_t total = a.ctrl->total_tiles;
     const int32_t nseg = a.ctrl->k * kNB;
+    const bool staged = nseg <= kSegSmem;
+    if (staged) {
+        for (int i = threadIdx.x; i <= nseg; i += kBlock) {
+            st.tile_prefix[i] = a.tile_prefix[i];
+            st.seg_start[i] = a.seg_start[i];
+        }
+    }
+    const int32_t* tp = staged ? st.tile_prefix : a.tile_prefix;
+    const int32_t* ss = staged ? st.seg_start : a.seg_start;
     int32_t my_max = 0;
     unsigned long long edges = 0;
     if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctrl->claim, 1);
@@ -419,10 +477,11 @@ __global__ void __launch_bounds__(kBlock) k_rc_recolor_dataflow(RcArgs a) {
         int32_t next = 0;
         if (threadIdx.x == 0) {
             next = atomicAdd(&a.ctrl->claim, 1);
-            s_seg = find_segment(a.tile_prefix, nseg, t);
+            s_seg = find_segment(tp, nseg, t);
         }
         __syncthreads();
-        recolor_tile<true>(a, sm, s_seg, t, my_max, edges);
+        const int32_t sg = s_seg;
+        recolor_tile<true>(a, sm, sg, ss[sg], ss[sg + 1], t - tp[sg], my_max, edges);
         __syncthreads();
         if (threadIdx.x == 0) s_tile = next;
         __syncthreads();
@@ -442,7 +501,8 @@ __global__ void __launch_bounds__(kBlock) k_rc_recolor_step(RcArgs a, int32_t p,
     for (int32_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
         int sg = seg0;
         while (sg + 1 < seg0 + kNB && a.tile_prefix[sg + 1] <= t) ++sg;
-        recolor_tile<false>(a, sm, sg, t, my_max, edges);
+        recolor_tile<false>(a, sm, sg, a.seg_start[sg], a.seg_start[sg + 1], t - a.tile_prefix[sg],
+                            my_max, edges);
     }
     warp_add(&a.ctrl->edges, edges);
     warp_max(&a.ncolors[a.iteration + 1], my_max);
@@ -459,6 +519,10 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
     const Tuning tune = current_tuning();
     const int grid = persistent_grid(tune);
     const int vgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, grid)));
+    const int grid_rc = resident_grid(k_rc_recolor_dataflow, tune);
+    const int grid_step = resident_grid(k_rc_recolor_step, tune);
+    const int grid_sc = static_cast<int>(std::max<int64_t>(
+        1, std::min<int64_t>((n + kBlock - 1) / kBlock, resident_grid(k_rc_scatter, tune))));
     cudaError_t ce;
 
     Scratch sc_ctrl, sc_bucket;
@@ -506,7 +570,8 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
         !sc_psize.alloc((cap + 1) * 4, s) || !sc_order.alloc((cap + 1) * 4, s) ||
         !sc_jtab.alloc((cap + 1) * 4, s) || !sc_rank.alloc((cap + 1) * 4, s) ||
         !sc_seg.alloc((ent + 1) * 4, s) || !sc_tiles.alloc((ent + 1) * 4, s) ||
-        !sc_fill.alloc(ent * 4, s) || !sc_list.alloc(n * 4, s) || !sc_alt.alloc(n * 4, s) ||
+        !sc_fill.alloc(ent * 4, s) || !sc_list.alloc(n * sizeof(WorkItem), s) ||
+        !sc_alt.alloc(n * 4, s) ||
         !sc_ncol.alloc((iterations + 1) * 4, s))
         return GC_ERR_OOM;
     a.cap = cap;
@@ -519,7 +584,7 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
     a.seg_start = sc_seg.as<int32_t>();
     a.tile_prefix = sc_tiles.as<int32_t>();
     a.fill = sc_fill.as<int32_t>();
-    a.list = sc_list.as<int32_t>();
+    a.list = sc_list.as<WorkItem>();
     a.ncolors = sc_ncol.as<int32_t>();
     cudaMemsetAsync(a.ncolors, 0, (iterations + 1) * 4, s);
 
@@ -539,9 +604,9 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
         cudaMemsetAsync(a.cls_cnt, 0, ent * 4, s);
         GC_LAUNCH(KID_RC_HIST, s, k_rc_hist<<<vgrid, kBlock, 0, s>>>(a));
         GC_LAUNCH(KID_RC_ORDER, s, k_rc_order<<<1, kOrderThreads, 0, s>>>(a));
-        GC_LAUNCH(KID_RC_SCATTER, s, k_rc_scatter<<<vgrid, kBlock, 0, s>>>(a));
+        GC_LAUNCH(KID_RC_SCATTER, s, k_rc_scatter<<<grid_sc, kBlock, 0, s>>>(a));
         if (tune.recolor_mode == 0) {
-            GC_LAUNCH(KID_RC_RECOLOR, s, k_rc_recolor_dataflow<<<grid, kBlock, 0, s>>>(a));
+            GC_LAUNCH(KID_RC_RECOLOR, s, k_rc_recolor_dataflow<<<grid_rc, kBlock, 0, s>>>(a));
         } else {
             RcCtrl hc;
             ce = cudaMemcpyAsync(&hc, a.ctrl, sizeof(RcCtrl), cudaMemcpyDeviceToHost, s);
@@ -553,7 +618,7 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
             for (int32_t p = 0; p < hc.k; ++p) {
                 const int32_t t0 = tp[p * kNB], t1 = tp[(p + 1) * kNB];
                 if (t1 <= t0) continue;
-                const int g2 = std::min(grid, t1 - t0);
+                const int g2 = std::min(grid_step, t1 - t0);
                 GC_LAUNCH(KID_RC_STEP, s, k_rc_recolor_step<<<g2, kBlock, 0, s>>>(a, p, t0, t1));
             }
         }

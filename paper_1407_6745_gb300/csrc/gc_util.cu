@@ -16,35 +16,125 @@ struct ValCtrl {
     int32_t max_color;
     uint32_t err;
     unsigned long long distinct;
+    int32_t heavy;          // rows deferred to the block-per-row pass
+    int32_t big_colors;     // vertices with a color >= kPresColors
 };
 
-__global__ void __launch_bounds__(kBlock) k_validate(Graph g, const int32_t* colors, ValCtrl* c) {
-    const int w = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * kBlock) >> 5;
-    const int l = lane_id();
-    int32_t my_max = 0;
-    unsigned long long conf = 0, unc = 0;
-    for (int64_t v = w; v < g.n; v += nw) {
-        const int32_t cv = colors[v];
-        int64_t beg, end;
-        row_range(g, static_cast<int32_t>(v), beg, end, &c->err);
-        int32_t mine = 0;
-        for (int64_t e = beg + l; e < end; e += 32) {
-            const int32_t u = load_nbr(g, e, &c->err);
-            if (u >= 0 && colors[u] == cv) ++mine;
+constexpr int kValG = 8;                 // lanes per light row
+constexpr int32_t kHeavyDeg = 256;       // heavier rows: one block each
+constexpr int kPresWords = 2048;         // presence bitmap of colors < 65536
+constexpr int32_t kPresColors = kPresWords * 32;
+
+struct ValArgs {
+    Graph g;
+    const int32_t* colors;
+    ValCtrl* c;
+    uint32_t* pres;    // kPresWords
+    int32_t* heavy;    // n
+};
+
+// Count of neighbors with v's color in this lane's stripe, U loads in flight.
+template <int U>
+__device__ __forceinline__ int32_t same_color(const ValArgs& a, int64_t beg, int32_t deg, int32_t cv,
+                                              int32_t lane0, int32_t stride) {
+    int32_t cnt = 0;
+    for (int32_t k0 = lane0; k0 < deg; k0 += stride * U) {
+        int32_t u[U], x[U];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const int32_t k = k0 + i * stride;
+            u[i] = k < deg ? load_nbr(a.g, beg + k, &a.c->err) : -1;
         }
 #pragma unroll
-        for (int d = 16; d >= 1; d >>= 1) mine += __shfl_xor_sync(kFull, mine, d);
-        if (l == 0) {
-            conf += static_cast<unsigned long long>(mine);
-            if (cv < 1) ++unc;
-            if (cv < 1 || mine > 0) atomicMin(&c->first_bad, static_cast<long long>(v));
-            my_max = max(my_max, cv);
+        for (int i = 0; i < U; ++i) x[i] = __ldg(a.colors + (u[i] >= 0 ? u[i] : 0));
+#pragma unroll
+        for (int i = 0; i < U; ++i) cnt += (u[i] >= 0 && x[i] == cv);
+    }
+    return cnt;
+}
+
+__device__ __forceinline__ void account(const ValArgs& a, int32_t v, int32_t cv, int32_t same,
+                                        uint32_t* s_pres, unsigned long long& conf,
+                                        unsigned long long& unc, int32_t& my_max) {
+    conf += static_cast<unsigned long long>(same);
+    if (cv < 1) ++unc;
+    if (cv < 1 || same > 0) atomicMin(&a.c->first_bad, static_cast<long long>(v));
+    my_max = max(my_max, cv);
+    if (cv >= 1 && cv < kPresColors) atomicOr(&s_pres[cv >> 5], 1u << (cv & 31));
+    else if (cv >= kPresColors) atomicAdd(&a.c->big_colors, 1);
+}
+
+__device__ __forceinline__ void flush_presence(const ValArgs& a, uint32_t* s_pres) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kPresWords; i += kBlock)
+        if (s_pres[i]) atomicOr(&a.pres[i], s_pres[i]);
+}
+
+// Light rows: 8 lanes per vertex; heavy rows are listed for the next pass.
+__global__ void __launch_bounds__(kBlock) k_validate(ValArgs a) {
+    __shared__ uint32_t s_pres[kPresWords];
+    for (int i = threadIdx.x; i < kPresWords; i += kBlock) s_pres[i] = 0u;
+    __syncthreads();
+    const int gi = threadIdx.x / kValG, gl = threadIdx.x % kValG;
+    const int64_t groups = static_cast<int64_t>(gridDim.x) * (kBlock / kValG);
+    int32_t my_max = 0;
+    unsigned long long conf = 0, unc = 0;
+    const int64_t n_pad = (a.g.n + groups - 1) / groups * groups;
+    for (int64_t v = static_cast<int64_t>(blockIdx.x) * (kBlock / kValG) + gi; v < n_pad; v += groups) {
+        const bool valid = v < a.g.n;
+        int64_t beg = 0;
+        int32_t deg = 0, cv = 0;
+        bool heavy = false;
+        if (valid) {
+            row_of(a.g, static_cast<int32_t>(v), beg, deg, &a.c->err);
+            cv = a.colors[v];
+            heavy = deg > kHeavyDeg;
+        }
+        int32_t same = same_color<4>(a, beg, heavy ? 0 : deg, cv, gl, kValG);
+#pragma unroll
+        for (int d = kValG / 2; d >= 1; d >>= 1) same += __shfl_xor_sync(kFull, same, d);
+        if (valid && gl == 0) {
+            if (heavy) a.heavy[atomicAdd(&a.c->heavy, 1)] = static_cast<int32_t>(v);
+            else account(a, static_cast<int32_t>(v), cv, same, s_pres, conf, unc, my_max);
         }
     }
-    warp_add(&c->conflicts, conf);
-    warp_add(&c->uncolored, unc);
-    warp_max(&c->max_color, my_max);
+    warp_add(&a.c->conflicts, conf);
+    warp_add(&a.c->uncolored, unc);
+    warp_max(&a.c->max_color, my_max);
+    flush_presence(a, s_pres);
+}
+
+// Heavy rows: one block per vertex.
+__global__ void __launch_bounds__(kBlock) k_validate_heavy(ValArgs a) {
+    __shared__ uint32_t s_pres[kPresWords];
+    __shared__ int32_t s_sum[kWarps];
+    for (int i = threadIdx.x; i < kPresWords; i += kBlock) s_pres[i] = 0u;
+    __syncthreads();
+    const int32_t nh = a.c->heavy;
+    int32_t my_max = 0;
+    unsigned long long conf = 0, unc = 0;
+    for (int32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+        const int32_t v = a.heavy[h];
+        int64_t beg;
+        int32_t deg;
+        row_of(a.g, v, beg, deg, &a.c->err);
+        const int32_t cv = a.colors[v];
+        int32_t same = same_color<4>(a, beg, deg, cv, threadIdx.x, kBlock);
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) same += __shfl_xor_sync(kFull, same, d);
+        if (lane_id() == 0) s_sum[threadIdx.x >> 5] = same;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t tot = 0;
+            for (int w = 0; w < kWarps; ++w) tot += s_sum[w];
+            account(a, v, cv, tot, s_pres, conf, unc, my_max);
+        }
+        __syncthreads();
+    }
+    warp_add(&a.c->conflicts, conf);
+    warp_add(&a.c->uncolored, unc);
+    warp_max(&a.c->max_color, my_max);
+    flush_presence(a, s_pres);
 }
 
 __global__ void __launch_bounds__(kBlock) k_mark_present(int64_t n, const int32_t* colors,
@@ -70,31 +160,38 @@ gc_status validate_device(const Graph& g, const int32_t* colors, gc_validation* 
     std::memset(out, 0, sizeof(*out));
     out->first_bad_vertex = -1;
     if (g.n == 0) return GC_OK;
-    Scratch sc;
-    if (!sc.alloc(sizeof(ValCtrl), s)) return GC_ERR_OOM;
-    ValCtrl* c = sc.as<ValCtrl>();
+    Scratch sc, sp, shv;
+    if (!sc.alloc(sizeof(ValCtrl), s) || !sp.alloc(kPresWords * 4, s) || !shv.alloc(g.n * 4, s))
+        return GC_ERR_OOM;
+    ValArgs a{g, colors, sc.as<ValCtrl>(), sp.as<uint32_t>(), shv.as<int32_t>()};
     ValCtrl h;
     std::memset(&h, 0, sizeof(h));
     h.first_bad = LLONG_MAX;
-    cudaMemcpyAsync(c, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(a.c, &h, sizeof(h), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(a.pres, 0, kPresWords * 4, s);
     const Tuning t = current_tuning();
     const int grid = persistent_grid(t);
-    GC_LAUNCH(KID_VALIDATE, s, k_validate<<<grid, kBlock, 0, s>>>(g, colors, c));
-    cudaError_t ce = cudaMemcpyAsync(&h, c, sizeof(h), cudaMemcpyDeviceToHost, s);
+    GC_LAUNCH(KID_VALIDATE, s, k_validate<<<resident_grid(k_validate, t), kBlock, 0, s>>>(a));
+    GC_LAUNCH(KID_VALIDATE_HEAVY, s,
+              k_validate_heavy<<<resident_grid(k_validate_heavy, t), kBlock, 0, s>>>(a));
+    GC_LAUNCH(KID_COUNT_BITS, s, k_count_bits<<<8, kBlock, 0, s>>>(kPresWords, a.pres, a.c));
+    cudaError_t ce = cudaMemcpyAsync(&h, a.c, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return cuda_status(ce);
     if (h.err & kErrBadGraph) return GC_ERR_BAD_GRAPH;
-    int64_t distinct = 0;
-    if (h.max_color >= 1) {
+    int64_t distinct = static_cast<int64_t>(h.distinct);
+    if (h.big_colors > 0) {
+        // colors beyond the shared bitmap: one bit per color up to the max
         const int64_t words = (static_cast<int64_t>(h.max_color) >> 5) + 1;
         Scratch sb;
         if (!sb.alloc(words * 4, s)) return GC_ERR_OOM;
         cudaMemsetAsync(sb.p, 0, words * 4, s);
+        cudaMemsetAsync(&a.c->distinct, 0, sizeof(unsigned long long), s);
         const int vg = static_cast<int>(std::min<int64_t>((g.n + kBlock - 1) / kBlock, grid));
         GC_LAUNCH(KID_MARK_PRESENT, s, k_mark_present<<<vg, kBlock, 0, s>>>(g.n, colors, sb.as<uint32_t>()));
         const int wg = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((words + kBlock - 1) / kBlock, grid)));
-        GC_LAUNCH(KID_COUNT_BITS, s, k_count_bits<<<wg, kBlock, 0, s>>>(words, sb.as<uint32_t>(), c));
-        ce = cudaMemcpyAsync(&h, c, sizeof(h), cudaMemcpyDeviceToHost, s);
+        GC_LAUNCH(KID_COUNT_BITS, s, k_count_bits<<<wg, kBlock, 0, s>>>(words, sb.as<uint32_t>(), a.c));
+        ce = cudaMemcpyAsync(&h, a.c, sizeof(h), cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) return cuda_status(ce);
         distinct = static_cast<int64_t>(h.distinct);
