@@ -270,7 +270,7 @@ def main():
     top_name, (top_launches, top_ms) = top
     per_launch_ms = top_ms / top_launches
     # algorithmic (compulsory) bytes per launch of the dominant kernel
-    if top_name == "k_rc_recolor_dataflow":
+    if top_name in ("k_rc_recolor_coop", "k_rc_recolor_step"):
         units = f"one recoloring iteration: every vertex once, nnz={nnz} entries"
         alg_bytes = 4 * nnz + 16 * n
     else:

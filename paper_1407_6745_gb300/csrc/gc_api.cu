@@ -113,7 +113,7 @@ namespace {
 const char* const kKernelNames[KID_COUNT_] = {
     "k_spec_setup", "k_spec_fill", "k_tentative", "k_conflict", "k_priorities",
     "k_rc_bucket", "k_rc_validate", "k_rc_hist", "k_rc_order", "k_rc_scatter",
-    "k_rc_recolor_dataflow", "k_rc_recolor_step", "k_validate", "k_validate_heavy",
+    "k_rc_recolor_coop", "k_rc_recolor_step", "k_validate", "k_validate_heavy",
     "k_mark_present", "k_count_bits", "k_check_graph"};
 std::atomic<bool> g_prof_on{false};
 std::mutex g_prof_mu;

@@ -14,17 +14,18 @@
 //                 rank of every color, segment starts and tile counts;
 //   k_rc_scatter  counting sort of the vertices into class-major,
 //                 bucket-minor segments; new[v] = -(rank(v) + 1);
-//   k_rc_recolor  the class steps.  Dataflow form: blocks claim tiles in
-//                 class order from an atomic counter; a neighbor u of an
+//   k_rc_recolor  the class steps, as one cooperative launch: warp tiles are
+//                 dealt out statically in class order; a neighbor u of an
 //                 earlier class whose new color is not yet written (still
 //                 negative) is waited for, with a bounded spin; a neighbor of
-//                 a later class (negative, rank above v's) is ignored.  All
-//                 earlier tiles were claimed by running blocks, and the
-//                 earliest unfinished tile waits on nothing, so the waits
-//                 always end.  The alternative form launches one grid per
-//                 class and needs no waits.
+//                 a later class (negative, rank above v's) is ignored.  The
+//                 alternative form launches one grid per class and needs no
+//                 waits.
 // The negative encoding makes one 4-byte gather per edge serve both "is u
-// earlier than v" and "what color did u take".
+// earlier than v" and "what color did u take".  Rows longer than
+// warp_max_deg are cut into chunks of 512 neighbors handled by different
+// warps; the chunks OR their forbidden colors into a per-row bitmap and the
+// warp that finishes the last chunk picks the color.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -36,14 +37,22 @@ namespace gc {
 constexpr int32_t kMaxInputColor = 1 << 28;
 constexpr int kOrderThreads = 1024;
 constexpr int kShuffleSmem = 4096;
+constexpr int32_t kChunk = 512;   // neighbors per chunk of a split (heavy) row
+
+// Vertices (or, bucket 0, row chunks) per warp tile.
+__host__ __device__ constexpr int warp_tile(int b) {
+    return b <= 2 ? 1 : b == 3 ? 2 : b == 4 ? 4 : 8;
+}
 
 struct RcCtrl {
     int32_t k;            // present classes this iteration
-    int32_t total_tiles;
-    int32_t claim;        // next tile to claim (dataflow)
+    int32_t total_tiles;  // warp tiles this iteration
+    int32_t hub_next;     // next free split-row slot
     int32_t max_deg;
     int32_t max_in;       // max input color (validation)
+    int32_t n_heavy;      // rows in bucket 0 (split into chunks)
     uint32_t err;
+    int32_t pad;
     unsigned long long edges;
 };
 
@@ -57,17 +66,23 @@ struct RcArgs {
     const int32_t* old_c;
     int32_t* new_c;
     uint8_t* bucket;
-    int32_t* cls_cnt;     // (cap + 1) * kNB
+    int32_t* cls_cnt;     // (cap + 1) * kNB vertices per (class, bucket)
+    int32_t* cls_units;   // cap + 1: row chunks of the bucket-0 vertices per class
     int32_t* present;     // cap + 1
     int32_t* psize;       // cap + 1
     int32_t* order;       // cap + 1 (class order, colors)
     int32_t* jtab;        // cap + 1 (shuffle indices)
     int32_t* rank_of;     // cap + 1
-    int32_t* seg_start;   // (cap + 1) * kNB + 1
-    int32_t* tile_prefix; // (cap + 1) * kNB + 1
+    int32_t* seg_start;   // (cap + 1) * kNB + 1, in list entries
+    int32_t* tile_prefix; // (cap + 1) * kNB + 1, in warp tiles
     int32_t* fill;        // (cap + 1) * kNB
-    WorkItem* list;       // n, vertices in class-major order
+    WorkItem* list;       // list entries in class-major order
     int32_t* ncolors;     // iterations + 1
+    int32_t* hub_v;       // split rows: vertex, chunk count, finished chunks,
+    int32_t* hub_nch;     //   and a forbidden-color bitmap of hub_words words
+    int32_t* hub_done;
+    uint32_t* hub_bm;
+    int32_t hub_words;
     RcCtrl* ctrl;
 };
 
@@ -80,21 +95,28 @@ __device__ __forceinline__ void st_relaxed(int32_t* p, int32_t x) {
     asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
 }
 
+__device__ __forceinline__ int32_t chunks_of(int32_t deg) { return (deg + kChunk - 1) / kChunk; }
+
 // ---------------------------------------------------------------------------
 // Per-call set-up: degree buckets (X = 1) and, for untrusted input, the
 // proper-coloring check of Sec. 1 plus the max color.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock) k_rc_bucket(RcArgs a) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * kBlock;
-    int32_t my_max = 0;
+    int32_t my_max = 0, heavy = 0;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; i < a.g.n; i += stride) {
-        int64_t beg, end;
-        row_range(a.g, static_cast<int32_t>(i), beg, end, &a.ctrl->err);
-        const int64_t deg = end - beg;
-        my_max = max(my_max, static_cast<int32_t>(deg < INT32_MAX ? deg : INT32_MAX));
-        a.bucket[i] = static_cast<uint8_t>(bucket_of(deg, 1, a.tune));
+        int64_t beg;
+        int32_t deg;
+        row_of(a.g, static_cast<int32_t>(i), beg, deg, &a.ctrl->err);
+        my_max = max(my_max, deg);
+        const int b = bucket_of(deg, 1, a.tune);
+        a.bucket[i] = static_cast<uint8_t>(b);
+        heavy += b == 0;
     }
     warp_max(&a.ctrl->max_deg, my_max);
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) heavy += __shfl_xor_sync(kFull, heavy, d);
+    if (lane_id() == 0 && heavy) atomicAdd(&a.ctrl->n_heavy, heavy);
 }
 
 __global__ void __launch_bounds__(kBlock) k_rc_validate(RcArgs a) {
@@ -109,11 +131,12 @@ __global__ void __launch_bounds__(kBlock) k_rc_validate(RcArgs a) {
             continue;
         }
         my_max = max(my_max, cv);
-        int64_t beg, end;
-        row_range(a.g, static_cast<int32_t>(v), beg, end, &a.ctrl->err);
+        int64_t beg;
+        int32_t deg;
+        row_of(a.g, static_cast<int32_t>(v), beg, deg, &a.ctrl->err);
         bool bad = false;
-        for (int64_t e = beg + l; e < end; e += 32) {
-            const int32_t u = load_nbr(a.g, e, &a.ctrl->err);
+        for (int32_t k = l; k < deg; k += 32) {
+            const int32_t u = load_nbr(a.g, beg + k, &a.ctrl->err);
             if (u >= 0 && a.old_c[u] == cv) bad = true;
         }
         if (__any_sync(kFull, bad) && l == 0) atomicOr(&a.ctrl->err, kErrImproper);
@@ -122,7 +145,7 @@ __global__ void __launch_bounds__(kBlock) k_rc_validate(RcArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Histogram of (class, bucket)
+// Histogram of (class, bucket); bucket-0 rows also count their chunks
 // ---------------------------------------------------------------------------
 constexpr int kHistSmem = 8192;
 
@@ -141,9 +164,20 @@ __global__ void __launch_bounds__(kBlock) k_rc_hist(RcArgs a) {
             atomicOr(&a.ctrl->err, kErrImproper);
             continue;
         }
-        const int32_t key = c * kNB + a.bucket[v];
-        if (local) atomicAdd(&sh[key], 1);
-        else atomicAdd(&a.cls_cnt[key], 1);
+        const int b = a.bucket[v];
+        const int32_t key = c * kNB + b;
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, key);
+        if (lane_id() == __ffs(peers) - 1) {
+            if (local) atomicAdd(&sh[key], __popc(peers));
+            else atomicAdd(&a.cls_cnt[key], __popc(peers));
+        }
+        if (b == 0) {
+            int64_t beg;
+            int32_t deg;
+            row_of(a.g, static_cast<int32_t>(v), beg, deg, &a.ctrl->err);
+            atomicAdd(&a.cls_units[c], chunks_of(deg));
+        }
     }
     if (local) {
         __syncthreads();
@@ -241,7 +275,8 @@ __global__ void __launch_bounds__(kOrderThreads) k_rc_order(RcArgs a) {
     }
     __syncthreads();
 
-    // rank of every present color; segments (class-major, bucket-minor)
+    // rank of every present color; segments (class-major, bucket-minor) in
+    // list entries and in warp tiles
     for (int32_t p = t; p < k; p += kOrderThreads) a.rank_of[a.order[p]] = p;
     const int32_t nseg = k * kNB;
     int32_t vbase = 0, tbase = 0;
@@ -250,8 +285,9 @@ __global__ void __launch_bounds__(kOrderThreads) k_rc_order(RcArgs a) {
         int32_t cnt = 0, tiles = 0;
         if (sg < nseg) {
             const int b = sg % kNB;
-            cnt = a.cls_cnt[a.order[sg / kNB] * kNB + b];
-            tiles = (cnt + bucket_tile(b) - 1) / bucket_tile(b);
+            const int32_t c = a.order[sg / kNB];
+            cnt = b == 0 ? a.cls_units[c] : a.cls_cnt[c * kNB + b];
+            tiles = (cnt + warp_tile(b) - 1) / warp_tile(b);
             a.fill[sg] = 0;
         }
         int32_t vt, tt;
@@ -269,29 +305,64 @@ __global__ void __launch_bounds__(kOrderThreads) k_rc_order(RcArgs a) {
         a.tile_prefix[nseg] = tbase;
         a.ctrl->k = k;
         a.ctrl->total_tiles = tbase;
-        a.ctrl->claim = 0;
+        a.ctrl->hub_next = 0;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Counting-sort scatter into class-major segments.  Each block takes a
-// contiguous slice of vertices, counts its vertices per segment in shared
-// memory, reserves its ranges with one global atomic per (block, segment),
-// then places the vertices.  (Order inside a segment is free: a class is an
+// contiguous slice of vertices, counts its list entries per segment in
+// shared memory, reserves its ranges with one global atomic per (block,
+// segment), then places them.  A bucket-0 row takes one entry per chunk and
+// a split-row slot.  (Order inside a segment is free: a class is an
 // independent set.)
 // ---------------------------------------------------------------------------
 constexpr int kScatterSegs = 4096;
 
-__device__ __forceinline__ int32_t segment_of(const RcArgs& a, int32_t v) {
-    return a.rank_of[a.old_c[v]] * kNB + a.bucket[v];
-}
-
-__device__ __forceinline__ void place(const RcArgs& a, int32_t v, int32_t sg, int32_t pos) {
+struct ScatterInfo {
+    int32_t sg;
+    int32_t units;
     int64_t beg;
     int32_t deg;
-    row_of(a.g, v, beg, deg, &a.ctrl->err);
-    store_item(a.list + pos, beg, v, deg);
-    a.new_c[v] = -(sg / kNB + 1);
+};
+
+__device__ __forceinline__ ScatterInfo scatter_info(const RcArgs& a, int32_t v) {
+    ScatterInfo si;
+    const int b = a.bucket[v];
+    si.sg = a.rank_of[a.old_c[v]] * kNB + b;
+    row_of(a.g, v, si.beg, si.deg, &a.ctrl->err);
+    si.units = b == 0 ? chunks_of(si.deg) : 1;
+    return si;
+}
+
+__device__ __forceinline__ void place(const RcArgs& a, int32_t v, const ScatterInfo& si, int32_t pos) {
+    a.new_c[v] = -(si.sg / kNB + 1);
+    if (si.sg % kNB != 0) {
+        store_item(a.list + pos, si.beg, v, si.deg);
+        return;
+    }
+    const int32_t slot = atomicAdd(&a.ctrl->hub_next, 1);
+    a.hub_v[slot] = v;
+    a.hub_nch[slot] = si.units;
+    a.hub_done[slot] = 0;
+    for (int32_t w = 0; w < a.hub_words; ++w) a.hub_bm[static_cast<int64_t>(slot) * a.hub_words + w] = 0u;
+    for (int32_t c = 0; c < si.units; ++c) {
+        const int32_t len = min(kChunk, si.deg - c * kChunk);
+        store_item(a.list + pos + c, si.beg + static_cast<int64_t>(c) * kChunk, -(slot + 1), len);
+    }
+}
+
+// Reserve `units` entries of segment sg from a counter (warp-aggregated
+// when all peers reserve one entry).
+__device__ __forceinline__ int32_t reserve(int32_t* counter_base, const ScatterInfo& si) {
+    if (si.units != 1) return atomicAdd(&counter_base[si.sg], si.units);
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, si.sg);
+    const int leader = __ffs(peers) - 1;
+    int32_t base = 0;
+    if (lane_id() == leader) base = atomicAdd(&counter_base[si.sg], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + __popc(peers & ((1u << lane_id()) - 1u));
 }
 
 __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
@@ -303,27 +374,20 @@ __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
     const int64_t lo = blockIdx.x * chunk;
     const int64_t hi = a.g.n < lo + chunk ? a.g.n : lo + chunk;
     if (nseg > kScatterSegs) {
-        // many classes: warp-aggregated global atomics
+        // many classes: global atomics
         for (int64_t i = lo + threadIdx.x; i < hi; i += kBlock) {
             const int32_t v = static_cast<int32_t>(i);
-            const int32_t sg = segment_of(a, v);
-            const unsigned act = __activemask();
-            const unsigned peers = __match_any_sync(act, sg);
-            const int leader = __ffs(peers) - 1;
-            int32_t base = 0;
-            if (lane_id() == leader) base = atomicAdd(&a.fill[sg], __popc(peers));
-            base = __shfl_sync(peers, base, leader);
-            place(a, v, sg, a.seg_start[sg] + base + __popc(peers & ((1u << lane_id()) - 1u)));
+            const ScatterInfo si = scatter_info(a, v);
+            const int32_t off = reserve(a.fill, si);
+            place(a, v, si, a.seg_start[si.sg] + off);
         }
         return;
     }
     for (int i = threadIdx.x; i < nseg; i += kBlock) s_cnt[i] = 0;
     __syncthreads();
     for (int64_t i = lo + threadIdx.x; i < hi; i += kBlock) {
-        const int32_t sg = segment_of(a, static_cast<int32_t>(i));
-        const unsigned act = __activemask();
-        const unsigned peers = __match_any_sync(act, sg);
-        if (lane_id() == __ffs(peers) - 1) atomicAdd(&s_cnt[sg], __popc(peers));
+        const ScatterInfo si = scatter_info(a, static_cast<int32_t>(i));
+        reserve(s_cnt, si);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nseg; i += kBlock) {
@@ -334,14 +398,9 @@ __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
     __syncthreads();
     for (int64_t i = lo + threadIdx.x; i < hi; i += kBlock) {
         const int32_t v = static_cast<int32_t>(i);
-        const int32_t sg = segment_of(a, v);
-        const unsigned act = __activemask();
-        const unsigned peers = __match_any_sync(act, sg);
-        const int leader = __ffs(peers) - 1;
-        int32_t base = 0;
-        if (lane_id() == leader) base = atomicAdd(&s_cnt[sg], __popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        place(a, v, sg, s_base[sg] + base + __popc(peers & ((1u << lane_id()) - 1u)));
+        const ScatterInfo si = scatter_info(a, v);
+        const int32_t off = reserve(s_cnt, si);
+        place(a, v, si, s_base[si.sg] + off);
     }
 }
 
@@ -379,16 +438,11 @@ struct RecolorFetch {
     }
 };
 
-union RcShared {
-    BlockScratch blk;
-    uint32_t warp_bm[kWarps][kWarpBitmapWords];
-};
-
 template <int G, bool kDataflow>
 __device__ __forceinline__ void recolor_group_tile(const RcArgs& a, const RecolorFetch<kDataflow>& f,
                                                    int32_t first, int32_t last, int32_t& my_max,
                                                    unsigned long long& edges) {
-    const int gi = threadIdx.x / G, gl = threadIdx.x % G;
+    const int gi = lane_id() / G, gl = lane_id() % G;
     const int32_t k = first + gi;
     const bool valid = k < last;
     WorkItem it{0, 0, 0};
@@ -401,36 +455,74 @@ __device__ __forceinline__ void recolor_group_tile(const RcArgs& a, const Recolo
     }
 }
 
+// One chunk of a split row: the chunk's forbidden colors are OR-ed into the
+// row's bitmap; the warp finishing the last chunk picks the First-Fit color.
 template <bool kDataflow>
-__device__ __forceinline__ void recolor_tile(const RcArgs& a, RcShared& sm, int32_t sg,
-                                             int32_t seg_first, int32_t seg_last, int32_t tile_in_seg,
-                                             int32_t& my_max, unsigned long long& edges) {
+__device__ __forceinline__ void recolor_chunk(const RcArgs& a, const RecolorFetch<kDataflow>& f,
+                                              const WorkItem& it, uint32_t* bm, int32_t& my_max,
+                                              unsigned long long& edges) {
+    const int l = lane_id();
+    const int32_t slot = -it.v - 1;
+    uint32_t* hb = a.hub_bm + static_cast<int64_t>(slot) * a.hub_words;
+    for (int32_t w0 = 0; w0 < a.hub_words; w0 += kWarpBitmapWords) {
+        bm[l] = 0u;
+        bm[l + 32] = 0u;
+        __syncwarp();
+        const int32_t base = w0 * 32 + 1;
+        scan_row<4>(a.g, it.beg, it.deg, l, 32, f,
+                    [&](int32_t c) {
+                        const uint32_t d = static_cast<uint32_t>(c - base);
+                        if (c > 0 && d < 32u * kWarpBitmapWords) atomicOr(&bm[d >> 5], 1u << (d & 31));
+                    },
+                    &a.ctrl->err);
+        __syncwarp();
+        for (int i = l; i < kWarpBitmapWords && w0 + i < a.hub_words; i += 32)
+            if (bm[i]) atomicOr(&hb[w0 + i], bm[i]);
+        __syncwarp();
+    }
+    if (l == 0) edges += static_cast<unsigned long long>(it.deg);
+    __threadfence();
+    int last = 0;
+    if (l == 0) last = atomicAdd(&a.hub_done[slot], 1) == a.hub_nch[slot] - 1;
+    last = __shfl_sync(kFull, last, 0);
+    if (!last) return;
+    __threadfence();
+    // First Fit over the merged bitmap: the first clear bit
+    for (int32_t w0 = 0; w0 < a.hub_words; w0 += 32) {
+        const int32_t i = w0 + l;
+        const uint32_t free_bits = i < a.hub_words ? ~__ldcg(hb + i) : 0u;
+        const uint32_t any = __ballot_sync(kFull, free_bits != 0u);
+        if (any) {
+            const int src = __ffs(any) - 1;
+            const uint32_t fw = __shfl_sync(kFull, free_bits, src);
+            const int32_t c = (w0 + src) * 32 + __ffs(fw);
+            if (l == 0) {
+                st_relaxed(a.new_c + a.hub_v[slot], c);
+                my_max = max(my_max, c);
+            }
+            return;
+        }
+    }
+}
+
+template <bool kDataflow>
+__device__ __forceinline__ void recolor_warp_tile(const RcArgs& a, uint32_t* bm, int32_t sg,
+                                                  int32_t seg_first, int32_t seg_last,
+                                                  int32_t tile_in_seg, int32_t& my_max,
+                                                  unsigned long long& edges) {
     const int32_t p = sg / kNB;
     const int b = sg % kNB;
-    const int32_t first = seg_first + tile_in_seg * bucket_tile(b);
+    const int32_t first = seg_first + tile_in_seg * warp_tile(b);
     const RecolorFetch<kDataflow> f{a.new_c, p, a.tune.spin_limit, &a.ctrl->err};
     switch (b) {
-    case 0: {
+    case 0: recolor_chunk<kDataflow>(a, f, load_item(a.list + first), bm, my_max, edges); break;
+    case 1: {
         const WorkItem it = load_item(a.list + first);
-        const int32_t c = choose_block<4>(a.g, it.beg, it.deg, 0u, f, sm.blk, &a.ctrl->err);
-        if (threadIdx.x == 0) {
+        const int32_t c = choose_warp<4>(a.g, it.beg, it.deg, 0u, f, bm, &a.ctrl->err);
+        if (lane_id() == 0) {
             st_relaxed(a.new_c + it.v, c);
             my_max = max(my_max, c);
             edges += static_cast<unsigned long long>(it.deg);
-        }
-        break;
-    }
-    case 1: {
-        const int w = threadIdx.x >> 5;
-        const int32_t k = first + w;
-        if (k < seg_last) {
-            const WorkItem it = load_item(a.list + k);
-            const int32_t c = choose_warp<4>(a.g, it.beg, it.deg, 0u, f, sm.warp_bm[w], &a.ctrl->err);
-            if (lane_id() == 0) {
-                st_relaxed(a.new_c + it.v, c);
-                my_max = max(my_max, c);
-                edges += static_cast<unsigned long long>(it.deg);
-            }
         }
         break;
     }
@@ -441,68 +533,57 @@ __device__ __forceinline__ void recolor_tile(const RcArgs& a, RcShared& sm, int3
     }
 }
 
-// Segment lookup: the segment table is staged in shared memory when it fits.
-constexpr int kSegSmem = 2048;
+// Segment table in shared memory when it fits.
+constexpr int kSegSmem = 1024;
 
-struct SegTable {
-    int32_t tile_prefix[kSegSmem + 1];
-    int32_t seg_start[kSegSmem + 1];
-};
-
-// Dataflow form: tiles claimed in class order; the next claim is taken while
-// the current tile is processed.
-__global__ void __launch_bounds__(kBlock) k_rc_recolor_dataflow(RcArgs a) {
-    __shared__ RcShared sm;
-    __shared__ SegTable st;
-    __shared__ int32_t s_tile, s_seg;
+// Dataflow form, cooperative launch (every block resident): warp w takes the
+// warp tiles w, w + W, w + 2W, ... in class order, W = all warps of the
+// grid.  A tile waits only on tiles before it, and the owner of the first
+// unfinished tile has finished all its earlier tiles, so it is working on
+// that tile: the waits always end.
+__global__ void __launch_bounds__(kBlock, 5) k_rc_recolor_coop(RcArgs a) {
+    __shared__ uint32_t s_bm[kWarps][kWarpBitmapWords];
+    __shared__ int32_t s_tp[kSegSmem + 1], s_ss[kSegSmem + 1];
     if (a.ctrl->err & (kErrImproper | kErrBadGraph)) return;
     const int32_t total = a.ctrl->total_tiles;
     const int32_t nseg = a.ctrl->k * kNB;
     const bool staged = nseg <= kSegSmem;
     if (staged) {
         for (int i = threadIdx.x; i <= nseg; i += kBlock) {
-            st.tile_prefix[i] = a.tile_prefix[i];
-            st.seg_start[i] = a.seg_start[i];
+            s_tp[i] = a.tile_prefix[i];
+            s_ss[i] = a.seg_start[i];
         }
     }
-    const int32_t* tp = staged ? st.tile_prefix : a.tile_prefix;
-    const int32_t* ss = staged ? st.seg_start : a.seg_start;
+    __syncthreads();
+    const int32_t* tp = staged ? s_tp : a.tile_prefix;
+    const int32_t* ss = staged ? s_ss : a.seg_start;
+    const int warp = threadIdx.x >> 5;
+    const int32_t W = gridDim.x * kWarps;
     int32_t my_max = 0;
     unsigned long long edges = 0;
-    if (threadIdx.x == 0) s_tile = atomicAdd(&a.ctrl->claim, 1);
-    __syncthreads();
-    for (;;) {
-        const int32_t t = s_tile;
-        if (t >= total) break;
-        int32_t next = 0;
-        if (threadIdx.x == 0) {
-            next = atomicAdd(&a.ctrl->claim, 1);
-            s_seg = find_segment(tp, nseg, t);
-        }
-        __syncthreads();
-        const int32_t sg = s_seg;
-        recolor_tile<true>(a, sm, sg, ss[sg], ss[sg + 1], t - tp[sg], my_max, edges);
-        __syncthreads();
-        if (threadIdx.x == 0) s_tile = next;
-        __syncthreads();
+    int32_t sg = 0;
+    for (int32_t t = blockIdx.x * kWarps + warp; t < total; t += W) {
+        if (tp[sg + 1] <= t) sg = find_segment(tp, nseg, t);
+        recolor_warp_tile<true>(a, s_bm[warp], sg, ss[sg], ss[sg + 1], t - tp[sg], my_max, edges);
     }
     warp_add(&a.ctrl->edges, edges);
     warp_max(&a.ncolors[a.iteration + 1], my_max);
 }
 
-// Stepwise form: one launch per class p over its tiles [t0, t1).
-__global__ void __launch_bounds__(kBlock) k_rc_recolor_step(RcArgs a, int32_t p, int32_t t0,
+// Stepwise form: one launch per class p over its warp tiles [t0, t1).
+__global__ void __launch_bounds__(kBlock, 5) k_rc_recolor_step(RcArgs a, int32_t p, int32_t t0,
                                                             int32_t t1) {
-    __shared__ RcShared sm;
+    __shared__ uint32_t s_bm[kWarps][kWarpBitmapWords];
     if (a.ctrl->err & (kErrImproper | kErrBadGraph)) return;
+    const int warp = threadIdx.x >> 5;
     int32_t my_max = 0;
     unsigned long long edges = 0;
     const int32_t seg0 = p * kNB;
-    for (int32_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
+    for (int32_t t = t0 + blockIdx.x * kWarps + warp; t < t1; t += gridDim.x * kWarps) {
         int sg = seg0;
         while (sg + 1 < seg0 + kNB && a.tile_prefix[sg + 1] <= t) ++sg;
-        recolor_tile<false>(a, sm, sg, a.seg_start[sg], a.seg_start[sg + 1], t - a.tile_prefix[sg],
-                            my_max, edges);
+        recolor_warp_tile<false>(a, s_bm[warp], sg, a.seg_start[sg], a.seg_start[sg + 1],
+                                 t - a.tile_prefix[sg], my_max, edges);
     }
     warp_add(&a.ctrl->edges, edges);
     warp_max(&a.ncolors[a.iteration + 1], my_max);
@@ -519,7 +600,8 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
     const Tuning tune = current_tuning();
     const int grid = persistent_grid(tune);
     const int vgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, grid)));
-    const int grid_rc = resident_grid(k_rc_recolor_dataflow, tune);
+    const int coop_capacity = sm_count() * occupancy_of(reinterpret_cast<const void*>(k_rc_recolor_coop), kBlock);
+    const int grid_rc = std::min(resident_grid(k_rc_recolor_coop, tune), coop_capacity);
     const int grid_step = resident_grid(k_rc_recolor_step, tune);
     const int grid_sc = static_cast<int>(std::max<int64_t>(
         1, std::min<int64_t>((n + kBlock - 1) / kBlock, resident_grid(k_rc_scatter, tune))));
@@ -562,20 +644,29 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
         return ce == cudaSuccess ? GC_OK : cuda_status(ce);
     }
 
-    const int32_t cap = std::max(maxc_in, h.max_deg + 1);
+    // Colors stay within [1, maxc_in]: a vertex of the class of rank p takes
+    // at most color p + 1 <= k <= maxc_in.
+    const int32_t cap = std::max(maxc_in, 1);
     const int64_t ent = static_cast<int64_t>(cap + 1) * kNB;
-    Scratch sc_cls, sc_present, sc_psize, sc_order, sc_jtab, sc_rank, sc_seg, sc_tiles, sc_fill,
-        sc_list, sc_alt, sc_ncol;
-    if (!sc_cls.alloc(ent * 4, s) || !sc_present.alloc((cap + 1) * 4, s) ||
-        !sc_psize.alloc((cap + 1) * 4, s) || !sc_order.alloc((cap + 1) * 4, s) ||
-        !sc_jtab.alloc((cap + 1) * 4, s) || !sc_rank.alloc((cap + 1) * 4, s) ||
-        !sc_seg.alloc((ent + 1) * 4, s) || !sc_tiles.alloc((ent + 1) * 4, s) ||
-        !sc_fill.alloc(ent * 4, s) || !sc_list.alloc(n * sizeof(WorkItem), s) ||
-        !sc_alt.alloc(n * 4, s) ||
-        !sc_ncol.alloc((iterations + 1) * 4, s))
+    const int32_t hub_words = (cap + 1 + 31) / 32;
+    const int64_t hubs = std::max<int64_t>(1, h.n_heavy);
+    Scratch sc_cls, sc_units, sc_present, sc_psize, sc_order, sc_jtab, sc_rank, sc_seg, sc_tiles,
+        sc_fill, sc_list, sc_alt, sc_ncol, sc_hv, sc_hn, sc_hd, sc_hb;
+    // list entries: one per vertex, one per chunk of a bucket-0 row
+    const int64_t list_len = n + (static_cast<int64_t>(g.nnz) / kChunk) + h.n_heavy;
+    if (!sc_cls.alloc(ent * 4, s) || !sc_units.alloc((cap + 1) * 4, s) ||
+        !sc_present.alloc((cap + 1) * 4, s) || !sc_psize.alloc((cap + 1) * 4, s) ||
+        !sc_order.alloc((cap + 1) * 4, s) || !sc_jtab.alloc((cap + 1) * 4, s) ||
+        !sc_rank.alloc((cap + 1) * 4, s) || !sc_seg.alloc((ent + 1) * 4, s) ||
+        !sc_tiles.alloc((ent + 1) * 4, s) || !sc_fill.alloc(ent * 4, s) ||
+        !sc_list.alloc(list_len * sizeof(WorkItem), s) || !sc_alt.alloc(n * 4, s) ||
+        !sc_ncol.alloc((iterations + 1) * 4, s) || !sc_hv.alloc(hubs * 4, s) ||
+        !sc_hn.alloc(hubs * 4, s) || !sc_hd.alloc(hubs * 4, s) ||
+        !sc_hb.alloc(hubs * hub_words * 4, s))
         return GC_ERR_OOM;
     a.cap = cap;
     a.cls_cnt = sc_cls.as<int32_t>();
+    a.cls_units = sc_units.as<int32_t>();
     a.present = sc_present.as<int32_t>();
     a.psize = sc_psize.as<int32_t>();
     a.order = sc_order.as<int32_t>();
@@ -586,6 +677,11 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
     a.fill = sc_fill.as<int32_t>();
     a.list = sc_list.as<WorkItem>();
     a.ncolors = sc_ncol.as<int32_t>();
+    a.hub_v = sc_hv.as<int32_t>();
+    a.hub_nch = sc_hn.as<int32_t>();
+    a.hub_done = sc_hd.as<int32_t>();
+    a.hub_bm = sc_hb.as<uint32_t>();
+    a.hub_words = hub_words;
     cudaMemsetAsync(a.ncolors, 0, (iterations + 1) * 4, s);
 
     cudaEvent_t e0, e1;
@@ -602,11 +698,17 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
         a.old_c = cur;
         a.new_c = dst;
         cudaMemsetAsync(a.cls_cnt, 0, ent * 4, s);
+        cudaMemsetAsync(a.cls_units, 0, (cap + 1) * 4, s);
         GC_LAUNCH(KID_RC_HIST, s, k_rc_hist<<<vgrid, kBlock, 0, s>>>(a));
         GC_LAUNCH(KID_RC_ORDER, s, k_rc_order<<<1, kOrderThreads, 0, s>>>(a));
         GC_LAUNCH(KID_RC_SCATTER, s, k_rc_scatter<<<grid_sc, kBlock, 0, s>>>(a));
         if (tune.recolor_mode == 0) {
-            GC_LAUNCH(KID_RC_RECOLOR, s, k_rc_recolor_dataflow<<<grid_rc, kBlock, 0, s>>>(a));
+            void* args[] = {&a};
+            cudaError_t le;
+            GC_LAUNCH(KID_RC_RECOLOR, s,
+                      le = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_rc_recolor_coop),
+                                                       dim3(grid_rc), dim3(kBlock), args, 0, s));
+            if (le != cudaSuccess) { st = cuda_status(le); break; }
         } else {
             RcCtrl hc;
             ce = cudaMemcpyAsync(&hc, a.ctrl, sizeof(RcCtrl), cudaMemcpyDeviceToHost, s);
@@ -618,7 +720,7 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
             for (int32_t p = 0; p < hc.k; ++p) {
                 const int32_t t0 = tp[p * kNB], t1 = tp[(p + 1) * kNB];
                 if (t1 <= t0) continue;
-                const int g2 = std::min(grid_step, t1 - t0);
+                const int g2 = std::min(grid_step, (t1 - t0 + kWarps - 1) / kWarps);
                 GC_LAUNCH(KID_RC_STEP, s, k_rc_recolor_step<<<g2, kBlock, 0, s>>>(a, p, t0, t1));
             }
         }
