@@ -45,10 +45,10 @@ std::atomic<long long> g_launches{0};
 std::mutex g_tune_mu;
 Tuning default_tuning() {
     Tuning t;
-    t.g4_max_deg = 4;
-    t.g8_max_deg = 8;
-    t.g16_max_deg = 16;
-    t.warp_max_deg = 2048;
+    t.g4_max_deg = 64;
+    t.g8_max_deg = 64;
+    t.g16_max_deg = 64;
+    t.warp_max_deg = 512;
     t.grid_blocks = 0;
     t.recolor_mode = 0;
     t.spin_limit = 1 << 20;

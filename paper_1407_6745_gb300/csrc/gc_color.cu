@@ -9,8 +9,10 @@
 // color, losers form W_{r+1}.  The vertex of W_r with the largest (priority,
 // id) always wins, so the loop ends within |V| rounds.
 //
-// Layout in HBM: colors int32[n] (the output, 0 = uncolored), tent int32[n],
-// prio uint32[n] (Philox, once per call), two work lists int32[n] used as
+// Layout in HBM: colors int32[n] (the output, 0 = uncolored), key uint64[n]
+// = (tentative color << 32 | priority), so one 8-byte gather gives conflict
+// detection both the color and the priority of a neighbor; two work lists of
+// 16-byte items (vertex, row start, degree) used as
 // ping-pong buffers, each cut into six degree-bucket regions whose starts are
 // fixed in round 0 (a loser stays in its bucket, so a region never
 // overflows).  All per-round state (round number, bucket counts) lives in a
@@ -44,8 +46,7 @@ struct SpecArgs {
     uint64_t seed;
     Tuning tune;
     int32_t* color;    // fixed colors (0 = in the work set)
-    int32_t* tent;     // tentative colors
-    uint32_t* prio;    // priorities
+    uint64_t* key;     // (tentative color << 32) | priority
     uint8_t* bucket;   // degree bucket per vertex
     WorkItem* list0;   // work lists (ping-pong), bucket regions
     WorkItem* list1;
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(kBlock) k_spec_setup(SpecArgs a) {
         my_max_deg = max(my_max_deg, deg);
         const int b = bucket_of(deg, a.X, a.tune);
         a.bucket[v] = static_cast<uint8_t>(b);
-        a.prio[v] = prio_of(a.seed, v);
+        a.key[v] = prio_of(a.seed, v);  // tentative color 0
         a.color[v] = 0;
         const unsigned act = __activemask();
         const unsigned peers = __match_any_sync(act, b);
@@ -149,6 +150,10 @@ struct SnapshotFetch {
 // ---------------------------------------------------------------------------
 // Tentative coloring of W_r against the snapshot `color`
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_tent(const SpecArgs& a, int32_t v, int32_t c) {
+    const uint64_t k = a.key[v];
+    a.key[v] = (static_cast<uint64_t>(static_cast<uint32_t>(c)) << 32) | (k & 0xFFFFFFFFull);
+}
 template <int G, bool kRXF>
 __device__ __forceinline__ void tentative_group_tile(const SpecArgs& a, const RoundTiles& rt,
                                                      const WorkItem* list, int b, int32_t first,
@@ -165,13 +170,13 @@ __device__ __forceinline__ void tentative_group_tile(const SpecArgs& a, const Ro
     const SnapshotFetch fetch{a.color};
     const int32_t c = choose_reg<G, LanesUnroll<G>::U>(a.g, it.beg, it.deg, gl, j, fetch, &a.ctrl->err);
     if (valid && gl == 0) {
-        a.tent[it.v] = c;
+        set_tent(a, it.v, c);
         edges += static_cast<unsigned long long>(it.deg);
     }
 }
 
 template <bool kRXF>
-__global__ void __launch_bounds__(kBlock) k_tentative(SpecArgs a) {
+__global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
     __shared__ SpecShared sm;
     __shared__ RoundTiles rt;
     const int32_t round = a.ctrl->round;
@@ -190,7 +195,7 @@ __global__ void __launch_bounds__(kBlock) k_tentative(SpecArgs a) {
             const uint32_t j = kRXF ? scale_index(rxf_word(a.seed, it.v, round), a.X) : 0u;
             const int32_t c = choose_block<4>(a.g, it.beg, it.deg, j, fetch, sm.blk, &a.ctrl->err);
             if (threadIdx.x == 0) {
-                a.tent[it.v] = c;
+                set_tent(a, it.v, c);
                 edges += static_cast<unsigned long long>(it.deg);
             }
             break;
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(kBlock) k_tentative(SpecArgs a) {
                 const uint32_t j = kRXF ? scale_index(rxf_word(a.seed, it.v, round), a.X) : 0u;
                 const int32_t c = choose_warp<4>(a.g, it.beg, it.deg, j, fetch, sm.warp_bm[w], &a.ctrl->err);
                 if (lane_id() == 0) {
-                    a.tent[it.v] = c;
+                    set_tent(a, it.v, c);
                     edges += static_cast<unsigned long long>(it.deg);
                 }
             }
@@ -221,32 +226,31 @@ __global__ void __launch_bounds__(kBlock) k_tentative(SpecArgs a) {
 // ---------------------------------------------------------------------------
 // Conflict detection; winners fix their color, losers go to W_{r+1}
 // ---------------------------------------------------------------------------
-// u beats v in the total order: larger priority, then larger id
-__device__ __forceinline__ bool beats(uint32_t pu, int32_t u, uint32_t pv, int32_t v) {
-    return pu > pv || (pu == pv && u > v);
-}
-
 // Does some neighbor in this lane's stripe have v's tentative color and a
-// larger (priority, id)?  U neighbor loads in flight per lane.
+// larger (priority, id)?  With equal tentative colors the 64-bit keys order
+// as the priorities; equal keys fall back to the id.  U gathers in flight.
 template <int U>
 __device__ __forceinline__ bool loses(const SpecArgs& a, const WorkItem& it, int32_t lane0,
                                       int32_t stride) {
     if (it.deg == 0) return false;
-    const int32_t tv = __ldg(a.tent + it.v);
-    const uint32_t pv = __ldg(a.prio + it.v);
+    const uint64_t kv = __ldg(reinterpret_cast<const unsigned long long*>(a.key) + it.v);
+    const uint32_t tv = static_cast<uint32_t>(kv >> 32);
     for (int32_t k0 = lane0; k0 < it.deg; k0 += stride * U) {
-        int32_t u[U], t[U];
+        int32_t u[U];
+        uint64_t ku[U];
 #pragma unroll
         for (int i = 0; i < U; ++i) {
             const int32_t k = k0 + i * stride;
             u[i] = k < it.deg ? load_nbr(a.g, it.beg + k, &a.ctrl->err) : -1;
         }
 #pragma unroll
-        for (int i = 0; i < U; ++i) t[i] = __ldg(a.tent + (u[i] >= 0 ? u[i] : 0));
+        for (int i = 0; i < U; ++i)
+            ku[i] = __ldg(reinterpret_cast<const unsigned long long*>(a.key) + (u[i] >= 0 ? u[i] : 0));
         bool lose = false;
 #pragma unroll
         for (int i = 0; i < U; ++i)
-            if (u[i] >= 0 && u[i] != it.v && t[i] == tv && beats(__ldg(a.prio + u[i]), u[i], pv, it.v))
+            if (u[i] >= 0 && u[i] != it.v && static_cast<uint32_t>(ku[i] >> 32) == tv &&
+                (ku[i] > kv || (ku[i] == kv && u[i] > it.v)))
                 lose = true;
         if (lose) return true;
     }
@@ -268,7 +272,7 @@ __device__ __forceinline__ void conflict_group_tile(const SpecArgs& a, const Rou
     if (leader) {
         edges += static_cast<unsigned long long>(it.deg);
         if (!lose) {
-            const int32_t c = __ldg(a.tent + it.v);
+            const int32_t c = static_cast<int32_t>(a.key[it.v] >> 32);
             a.color[it.v] = c;
             my_max = max(my_max, c);
         }
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(kBlock) k_conflict(SpecArgs a) {
                     const int32_t pos = atomicAdd(&a.ctrl->cnt[par ^ 1][0], 1);
                     store_item(next + rt.start[0] + pos, it.beg, it.v, it.deg);
                 } else {
-                    const int32_t c = a.tent[it.v];
+                    const int32_t c = static_cast<int32_t>(a.key[it.v] >> 32);
                     a.color[it.v] = c;
                     my_max = max(my_max, c);
                 }
@@ -366,8 +370,8 @@ gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors
     }
     if (!t_pinned.p) return GC_ERR_OOM;
     const int64_t n = g.n;
-    Scratch sc_tent, sc_prio, sc_l0, sc_l1, sc_bucket, sc_ctrl;
-    if (!sc_tent.alloc(n * 4, s) || !sc_prio.alloc(n * 4, s) ||
+    Scratch sc_key, sc_l0, sc_l1, sc_bucket, sc_ctrl;
+    if (!sc_key.alloc(n * 8, s) ||
         !sc_l0.alloc(n * sizeof(WorkItem), s) || !sc_l1.alloc(n * sizeof(WorkItem), s) ||
         !sc_bucket.alloc(n, s) || !sc_ctrl.alloc(sizeof(SpecCtrl), s))
         return GC_ERR_OOM;
@@ -377,8 +381,7 @@ gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors
     a.seed = seed;
     a.tune = current_tuning();
     a.color = colors_out;
-    a.tent = sc_tent.as<int32_t>();
-    a.prio = sc_prio.as<uint32_t>();
+    a.key = sc_key.as<uint64_t>();
     a.bucket = sc_bucket.as<uint8_t>();
     a.list0 = sc_l0.as<WorkItem>();
     a.list1 = sc_l1.as<WorkItem>();

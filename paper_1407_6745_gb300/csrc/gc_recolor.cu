@@ -7,8 +7,9 @@
 // class is an independent set, so all its vertices can choose at once and
 // the result equals the sequential greedy run in class order (Sec. 3).
 //
-// One iteration = four launches, with no host round trip:
-//   k_rc_hist     histogram of (class, degree bucket) pairs;
+// One iteration = three launches, with no host round trip:
+//   k_rc_hist     histogram of (class, degree bucket) pairs (first iteration
+//                 only; later ones get it from the previous recoloring);
 //   k_rc_order    the class permutation, computed on the device (one block):
 //                 present classes, RV/NI/ND order or a Fisher-Yates shuffle,
 //                 rank of every color, segment starts and tile counts;
@@ -68,6 +69,8 @@ struct RcArgs {
     uint8_t* bucket;
     int32_t* cls_cnt;     // (cap + 1) * kNB vertices per (class, bucket)
     int32_t* cls_units;   // cap + 1: row chunks of the bucket-0 vertices per class
+    int32_t* nxt_cnt;     // the same two histograms of the new colors, filled by
+    int32_t* nxt_units;   //   the recoloring kernel for the next iteration
     int32_t* present;     // cap + 1
     int32_t* psize;       // cap + 1
     int32_t* order;       // cap + 1 (class order, colors)
@@ -438,9 +441,28 @@ struct RecolorFetch {
     }
 };
 
+// Histogram of the new colors for the next iteration: shared-memory counts
+// when they fit, flushed once per block.
+constexpr int kRcHistSmem = 2048;
+
+struct NextHist {
+    int32_t* sh;     // nullptr: count in global memory
+    int32_t* glob;
+    int32_t* units;
+    int32_t cap;
+    __device__ __forceinline__ void add(int32_t c, int b, int32_t chunks) const {
+        if (c < 1 || c > cap) return;
+        const int32_t key = c * kNB + b;
+        if (sh) atomicAdd(&sh[key], 1);
+        else atomicAdd(&glob[key], 1);
+        if (b == 0) atomicAdd(&units[c], chunks);
+    }
+};
+
 template <int G, bool kDataflow>
 __device__ __forceinline__ void recolor_group_tile(const RcArgs& a, const RecolorFetch<kDataflow>& f,
-                                                   int32_t first, int32_t last, int32_t& my_max,
+                                                   const NextHist& nh, int b, int32_t first,
+                                                   int32_t last, int32_t& my_max,
                                                    unsigned long long& edges) {
     const int gi = lane_id() / G, gl = lane_id() % G;
     const int32_t k = first + gi;
@@ -452,6 +474,7 @@ __device__ __forceinline__ void recolor_group_tile(const RcArgs& a, const Recolo
         st_relaxed(a.new_c + it.v, c);
         my_max = max(my_max, c);
         edges += static_cast<unsigned long long>(it.deg);
+        nh.add(c, b, 0);
     }
 }
 
@@ -459,8 +482,8 @@ __device__ __forceinline__ void recolor_group_tile(const RcArgs& a, const Recolo
 // row's bitmap; the warp finishing the last chunk picks the First-Fit color.
 template <bool kDataflow>
 __device__ __forceinline__ void recolor_chunk(const RcArgs& a, const RecolorFetch<kDataflow>& f,
-                                              const WorkItem& it, uint32_t* bm, int32_t& my_max,
-                                              unsigned long long& edges) {
+                                              const NextHist& nh, const WorkItem& it, uint32_t* bm,
+                                              int32_t& my_max, unsigned long long& edges) {
     const int l = lane_id();
     const int32_t slot = -it.v - 1;
     uint32_t* hb = a.hub_bm + static_cast<int64_t>(slot) * a.hub_words;
@@ -499,6 +522,7 @@ __device__ __forceinline__ void recolor_chunk(const RcArgs& a, const RecolorFetc
             if (l == 0) {
                 st_relaxed(a.new_c + a.hub_v[slot], c);
                 my_max = max(my_max, c);
+                nh.add(c, 0, a.hub_nch[slot]);
             }
             return;
         }
@@ -506,8 +530,8 @@ __device__ __forceinline__ void recolor_chunk(const RcArgs& a, const RecolorFetc
 }
 
 template <bool kDataflow>
-__device__ __forceinline__ void recolor_warp_tile(const RcArgs& a, uint32_t* bm, int32_t sg,
-                                                  int32_t seg_first, int32_t seg_last,
+__device__ __forceinline__ void recolor_warp_tile(const RcArgs& a, const NextHist& nh, uint32_t* bm,
+                                                  int32_t sg, int32_t seg_first, int32_t seg_last,
                                                   int32_t tile_in_seg, int32_t& my_max,
                                                   unsigned long long& edges) {
     const int32_t p = sg / kNB;
@@ -515,7 +539,7 @@ __device__ __forceinline__ void recolor_warp_tile(const RcArgs& a, uint32_t* bm,
     const int32_t first = seg_first + tile_in_seg * warp_tile(b);
     const RecolorFetch<kDataflow> f{a.new_c, p, a.tune.spin_limit, &a.ctrl->err};
     switch (b) {
-    case 0: recolor_chunk<kDataflow>(a, f, load_item(a.list + first), bm, my_max, edges); break;
+    case 0: recolor_chunk<kDataflow>(a, f, nh, load_item(a.list + first), bm, my_max, edges); break;
     case 1: {
         const WorkItem it = load_item(a.list + first);
         const int32_t c = choose_warp<4>(a.g, it.beg, it.deg, 0u, f, bm, &a.ctrl->err);
@@ -523,13 +547,14 @@ __device__ __forceinline__ void recolor_warp_tile(const RcArgs& a, uint32_t* bm,
             st_relaxed(a.new_c + it.v, c);
             my_max = max(my_max, c);
             edges += static_cast<unsigned long long>(it.deg);
+            nh.add(c, 1, 0);
         }
         break;
     }
-    case 2: recolor_group_tile<32, kDataflow>(a, f, first, seg_last, my_max, edges); break;
-    case 3: recolor_group_tile<16, kDataflow>(a, f, first, seg_last, my_max, edges); break;
-    case 4: recolor_group_tile<8, kDataflow>(a, f, first, seg_last, my_max, edges); break;
-    default: recolor_group_tile<4, kDataflow>(a, f, first, seg_last, my_max, edges); break;
+    case 2: recolor_group_tile<32, kDataflow>(a, f, nh, 2, first, seg_last, my_max, edges); break;
+    case 3: recolor_group_tile<16, kDataflow>(a, f, nh, 3, first, seg_last, my_max, edges); break;
+    case 4: recolor_group_tile<8, kDataflow>(a, f, nh, 4, first, seg_last, my_max, edges); break;
+    default: recolor_group_tile<4, kDataflow>(a, f, nh, 5, first, seg_last, my_max, edges); break;
     }
 }
 
@@ -541,9 +566,26 @@ constexpr int kSegSmem = 1024;
 // grid.  A tile waits only on tiles before it, and the owner of the first
 // unfinished tile has finished all its earlier tiles, so it is working on
 // that tile: the waits always end.
+__device__ __forceinline__ NextHist setup_next_hist(const RcArgs& a, int32_t* s_hist) {
+    const int32_t entries = (a.cap + 1) * kNB;
+    const bool local = entries <= kRcHistSmem;
+    if (local)
+        for (int i = threadIdx.x; i < entries; i += kBlock) s_hist[i] = 0;
+    return NextHist{local ? s_hist : nullptr, a.nxt_cnt, a.nxt_units, a.cap};
+}
+
+__device__ __forceinline__ void flush_next_hist(const RcArgs& a, const NextHist& nh) {
+    if (!nh.sh) return;
+    __syncthreads();
+    const int32_t entries = (a.cap + 1) * kNB;
+    for (int i = threadIdx.x; i < entries; i += kBlock)
+        if (nh.sh[i]) atomicAdd(&a.nxt_cnt[i], nh.sh[i]);
+}
+
 __global__ void __launch_bounds__(kBlock, 5) k_rc_recolor_coop(RcArgs a) {
     __shared__ uint32_t s_bm[kWarps][kWarpBitmapWords];
     __shared__ int32_t s_tp[kSegSmem + 1], s_ss[kSegSmem + 1];
+    __shared__ int32_t s_hist[kRcHistSmem];
     if (a.ctrl->err & (kErrImproper | kErrBadGraph)) return;
     const int32_t total = a.ctrl->total_tiles;
     const int32_t nseg = a.ctrl->k * kNB;
@@ -554,6 +596,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_rc_recolor_coop(RcArgs a) {
             s_ss[i] = a.seg_start[i];
         }
     }
+    const NextHist nh = setup_next_hist(a, s_hist);
     __syncthreads();
     const int32_t* tp = staged ? s_tp : a.tile_prefix;
     const int32_t* ss = staged ? s_ss : a.seg_start;
@@ -564,17 +607,21 @@ __global__ void __launch_bounds__(kBlock, 5) k_rc_recolor_coop(RcArgs a) {
     int32_t sg = 0;
     for (int32_t t = blockIdx.x * kWarps + warp; t < total; t += W) {
         if (tp[sg + 1] <= t) sg = find_segment(tp, nseg, t);
-        recolor_warp_tile<true>(a, s_bm[warp], sg, ss[sg], ss[sg + 1], t - tp[sg], my_max, edges);
+        recolor_warp_tile<true>(a, nh, s_bm[warp], sg, ss[sg], ss[sg + 1], t - tp[sg], my_max, edges);
     }
     warp_add(&a.ctrl->edges, edges);
     warp_max(&a.ncolors[a.iteration + 1], my_max);
+    flush_next_hist(a, nh);
 }
 
 // Stepwise form: one launch per class p over its warp tiles [t0, t1).
 __global__ void __launch_bounds__(kBlock, 5) k_rc_recolor_step(RcArgs a, int32_t p, int32_t t0,
-                                                            int32_t t1) {
+                                                               int32_t t1) {
     __shared__ uint32_t s_bm[kWarps][kWarpBitmapWords];
+    __shared__ int32_t s_hist[kRcHistSmem];
     if (a.ctrl->err & (kErrImproper | kErrBadGraph)) return;
+    const NextHist nh = setup_next_hist(a, s_hist);
+    __syncthreads();
     const int warp = threadIdx.x >> 5;
     int32_t my_max = 0;
     unsigned long long edges = 0;
@@ -582,11 +629,12 @@ __global__ void __launch_bounds__(kBlock, 5) k_rc_recolor_step(RcArgs a, int32_t
     for (int32_t t = t0 + blockIdx.x * kWarps + warp; t < t1; t += gridDim.x * kWarps) {
         int sg = seg0;
         while (sg + 1 < seg0 + kNB && a.tile_prefix[sg + 1] <= t) ++sg;
-        recolor_warp_tile<false>(a, s_bm[warp], sg, a.seg_start[sg], a.seg_start[sg + 1],
+        recolor_warp_tile<false>(a, nh, s_bm[warp], sg, a.seg_start[sg], a.seg_start[sg + 1],
                                  t - a.tile_prefix[sg], my_max, edges);
     }
     warp_add(&a.ctrl->edges, edges);
     warp_max(&a.ncolors[a.iteration + 1], my_max);
+    flush_next_hist(a, nh);
 }
 
 // ---------------------------------------------------------------------------
@@ -650,11 +698,12 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
     const int64_t ent = static_cast<int64_t>(cap + 1) * kNB;
     const int32_t hub_words = (cap + 1 + 31) / 32;
     const int64_t hubs = std::max<int64_t>(1, h.n_heavy);
-    Scratch sc_cls, sc_units, sc_present, sc_psize, sc_order, sc_jtab, sc_rank, sc_seg, sc_tiles,
+    Scratch sc_cls, sc_units, sc_cls2, sc_units2, sc_present, sc_psize, sc_order, sc_jtab, sc_rank, sc_seg, sc_tiles,
         sc_fill, sc_list, sc_alt, sc_ncol, sc_hv, sc_hn, sc_hd, sc_hb;
     // list entries: one per vertex, one per chunk of a bucket-0 row
     const int64_t list_len = n + (static_cast<int64_t>(g.nnz) / kChunk) + h.n_heavy;
     if (!sc_cls.alloc(ent * 4, s) || !sc_units.alloc((cap + 1) * 4, s) ||
+        !sc_cls2.alloc(ent * 4, s) || !sc_units2.alloc((cap + 1) * 4, s) ||
         !sc_present.alloc((cap + 1) * 4, s) || !sc_psize.alloc((cap + 1) * 4, s) ||
         !sc_order.alloc((cap + 1) * 4, s) || !sc_jtab.alloc((cap + 1) * 4, s) ||
         !sc_rank.alloc((cap + 1) * 4, s) || !sc_seg.alloc((ent + 1) * 4, s) ||
@@ -665,8 +714,6 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
         !sc_hb.alloc(hubs * hub_words * 4, s))
         return GC_ERR_OOM;
     a.cap = cap;
-    a.cls_cnt = sc_cls.as<int32_t>();
-    a.cls_units = sc_units.as<int32_t>();
     a.present = sc_present.as<int32_t>();
     a.psize = sc_psize.as<int32_t>();
     a.order = sc_order.as<int32_t>();
@@ -697,9 +744,19 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
         a.iteration = it;
         a.old_c = cur;
         a.new_c = dst;
-        cudaMemsetAsync(a.cls_cnt, 0, ent * 4, s);
-        cudaMemsetAsync(a.cls_units, 0, (cap + 1) * 4, s);
-        GC_LAUNCH(KID_RC_HIST, s, k_rc_hist<<<vgrid, kBlock, 0, s>>>(a));
+        // histograms: of the input (iteration 0), else filled by the previous
+        // iteration's recoloring kernel
+        a.cls_cnt = (it % 2 == 0) ? sc_cls.as<int32_t>() : sc_cls2.as<int32_t>();
+        a.cls_units = (it % 2 == 0) ? sc_units.as<int32_t>() : sc_units2.as<int32_t>();
+        a.nxt_cnt = (it % 2 == 0) ? sc_cls2.as<int32_t>() : sc_cls.as<int32_t>();
+        a.nxt_units = (it % 2 == 0) ? sc_units2.as<int32_t>() : sc_units.as<int32_t>();
+        if (it == 0) {
+            cudaMemsetAsync(a.cls_cnt, 0, ent * 4, s);
+            cudaMemsetAsync(a.cls_units, 0, (cap + 1) * 4, s);
+            GC_LAUNCH(KID_RC_HIST, s, k_rc_hist<<<vgrid, kBlock, 0, s>>>(a));
+        }
+        cudaMemsetAsync(a.nxt_cnt, 0, ent * 4, s);
+        cudaMemsetAsync(a.nxt_units, 0, (cap + 1) * 4, s);
         GC_LAUNCH(KID_RC_ORDER, s, k_rc_order<<<1, kOrderThreads, 0, s>>>(a));
         GC_LAUNCH(KID_RC_SCATTER, s, k_rc_scatter<<<grid_sc, kBlock, 0, s>>>(a));
         if (tune.recolor_mode == 0) {

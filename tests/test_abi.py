@@ -58,4 +58,4 @@ def test_argument_checks_need_no_gpu():
     with pytest.raises(gc.GCError):
         gc.gc_set_tuning(g4_max_deg=9, g8_max_deg=8)
     gc.gc_set_tuning()
-    assert gc.gc_get_tuning()["warp_max_deg"] == 2048
+    assert gc.gc_get_tuning()["warp_max_deg"] == 512
