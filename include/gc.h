@@ -161,6 +161,28 @@ gc_status gc_priorities(uint64_t seed, int64_t n, uint32_t* out, void* stream);
  * structure (GC_ERR_BAD_GRAPH if malformed). */
 gc_status gc_validate(const gc_graph* g, const int32_t* colors, gc_validation* out, void* stream);
 
+/*
+ * gc_validate that allocates nothing (the paper has no counterpart: this is
+ * a library convenience).  For callers that cannot allocate device memory --
+ * code running while a stream is being captured into a CUDA graph, a caller
+ * whose allocator is locked or exhausted, a latency-critical path that must
+ * not wait on the driver's allocator -- the call uses a fixed scratch array
+ * of about 8.3 KB in the library's static device memory instead of the pool;
+ * every GPU that loads libgc.so holds that array until the process exits.
+ *   - Same result as gc_validate; the graph and colors must be device memory
+ *     (GC_MEM_HOST is rejected with GC_ERR_INVALID_ARG: staging would allocate).
+ *   - Colors must be below 65536: the array's presence bitmap counts distinct
+ *     colors up to there; a larger color gives GC_ERR_INVALID_ARG.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call outside any stream capture.
+ *   - All calls share the array, which each call clears before use; calls
+ *     that overlap on the GPU (two streams, two host threads) race on it and
+ *     must be serialised by the caller.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+gc_status gc_validate_noalloc(const gc_graph* g, const int32_t* colors, gc_validation* out,
+                              void* stream);
+
 /* Structure check of a CSR: offsets start at 0, never decrease, end at nnz;
  * ids in [0, n); no self-loop.  GC_OK or GC_ERR_BAD_GRAPH; first_bad_vertex
  * (may be NULL) receives the smallest offending row, or -1. */

@@ -20,7 +20,8 @@ import torch
 
 __all__ = [
     "GCError", "FIRST_FIT", "RANDOM_X_FIT", "PERM", "library_path", "load",
-    "gc_color", "gc_recolor", "gc_color_recolor", "gc_validate", "gc_check_graph",
+    "gc_color", "gc_recolor", "gc_color_recolor", "gc_validate", "gc_validate_noalloc",
+    "gc_check_graph",
     "gc_priorities", "gc_set_tuning", "gc_get_tuning", "gc_profile_enable", "gc_profile_read",
     "gc_kernel_launches", "gc_status_string", "gc_version",
 ]
@@ -96,12 +97,15 @@ def load():
                                          ctypes.c_int, ctypes.c_int32, ctypes.c_uint64, P, P, S,
                                          ctypes.POINTER(_Validation), P]
         lib.gc_validate.argtypes = [G, P, ctypes.POINTER(_Validation), P]
+        lib.gc_validate_noalloc.argtypes = [G, P, ctypes.POINTER(_Validation), P]
+        lib.gc_validate_noalloc.restype = ctypes.c_int
         lib.gc_check_graph.argtypes = [G, ctypes.POINTER(ctypes.c_int64), P]
         lib.gc_priorities.argtypes = [ctypes.c_uint64, ctypes.c_int64, P, P]
         lib.gc_priorities.restype = ctypes.c_int
         lib.gc_set_tuning.argtypes = [ctypes.POINTER(_Tuning)]
         lib.gc_get_tuning.argtypes = [ctypes.POINTER(_Tuning)]
-        for f in ("gc_color", "gc_recolor", "gc_color_recolor", "gc_validate", "gc_check_graph",
+        for f in ("gc_color", "gc_recolor", "gc_color_recolor", "gc_validate", "gc_validate_noalloc",
+    "gc_check_graph",
                   "gc_priorities", "gc_set_tuning", "gc_get_tuning"):
             getattr(lib, f).restype = ctypes.c_int
         lib.gc_kernel_launches.restype = ctypes.c_int64
@@ -233,6 +237,20 @@ def gc_validate(offsets, idx, colors, stream=None):
     v = _Validation()
     _check(lib.gc_validate(ctypes.byref(g), _ptr(colors), ctypes.byref(v), _stream(dev, stream)),
            "gc_validate")
+    return {k: getattr(v, k) for k, _ in _Validation._fields_}
+
+
+def gc_validate_noalloc(offsets, idx, colors, stream=None):
+    """gc_validate without any device allocation (fixed scratch in the
+    library's static device memory; device tensors only, colors < 65536;
+    concurrent calls on the GPU must be serialised by the caller)."""
+    lib = load()
+    g, keep = _graph(offsets, idx)
+    dev = keep[0].device
+    _check_colors(colors, g.n, dev, "colors")
+    v = _Validation()
+    _check(lib.gc_validate_noalloc(ctypes.byref(g), _ptr(colors), ctypes.byref(v),
+                                   _stream(dev, stream)), "gc_validate_noalloc")
     return {k: getattr(v, k) for k, _ in _Validation._fields_}
 
 

@@ -420,6 +420,19 @@ int32_t gc_profile_read(gc_kernel_time* out, int32_t max) {
     return cnt;
 }
 
+gc_status gc_validate_noalloc(const gc_graph* g, const int32_t* colors, gc_validation* out,
+                              void* stream) {
+    gc_status st = check_graph_args(g);
+    if (st != GC_OK) return st;
+    if (g->mem != GC_MEM_DEVICE || !out || (g->n > 0 && !colors)) return GC_ERR_INVALID_ARG;
+    Graph dg;
+    dg.n = static_cast<int32_t>(g->n);
+    dg.nnz = g->nnz;
+    dg.off = g->offsets;
+    dg.idx = g->idx;
+    return validate_noalloc_device(dg, colors, out, static_cast<cudaStream_t>(stream));
+}
+
 gc_status gc_set_tuning(const gc_tuning* t) {
     Tuning v = default_tuning();
     if (t) {

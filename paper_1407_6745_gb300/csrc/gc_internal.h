@@ -94,6 +94,9 @@ gc_status priorities_device(uint64_t seed, int64_t n, uint32_t* out, cudaStream_
 gc_status validate_device(const Graph& g, const int32_t* colors, gc_validation* out,
                           cudaStream_t s);
 
+gc_status validate_noalloc_device(const Graph& g, const int32_t* colors, gc_validation* out,
+                                  cudaStream_t s);
+
 gc_status check_graph_device(const Graph& g, int64_t* first_bad, cudaStream_t s);
 
 }  // namespace gc

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <mutex>
 
 #include "gc_internal.h"
 
@@ -200,6 +201,189 @@ gc_status validate_device(const Graph& g, const int32_t* colors, gc_validation* 
     out->n_uncolored = static_cast<int64_t>(h.uncolored);
     out->max_color = h.max_color;
     out->n_distinct = static_cast<int32_t>(distinct);
+    out->first_bad_vertex = h.first_bad == LLONG_MAX ? -1 : static_cast<int64_t>(h.first_bad);
+    return GC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Validation without allocation (gc_validate_noalloc).  For callers that
+// must not allocate device memory: code that runs while a CUDA stream is
+// being captured into a graph (where a cudaMalloc would break the capture),
+// a caller whose allocator is locked or already exhausted, or a real-time
+// path that must not stall on the driver's allocator.  Its scratch is a
+// file-scope device array, held by every device that loads the library
+// until the process exits; every call shares it, so two calls that overlap
+// on the GPU (e.g. on two streams) race on it and must be serialised by
+// the caller.  The presence bitmap covers colors below kPresColors (65536);
+// a coloring with a larger color is rejected, since counting its distinct
+// colors would need scratch beyond the array.
+// ---------------------------------------------------------------------------
+struct NoAllocScratch {
+    ValCtrl ctrl;
+    uint32_t pres[kPresWords];
+};
+
+static __device__ __align__(256) NoAllocScratch g_validate_scratch;
+
+// Clears what every call must start from: counters, the first bad vertex
+// (LLONG_MAX = none yet) and the presence bitmap.
+__global__ void __launch_bounds__(kBlock) k_validate_na_clear(NoAllocScratch* sc) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->ctrl.conflicts = 0;
+        sc->ctrl.uncolored = 0;
+        sc->ctrl.first_bad = LLONG_MAX;
+        sc->ctrl.max_color = 0;
+        sc->ctrl.err = 0;
+        sc->ctrl.distinct = 0;
+        sc->ctrl.heavy = 0;
+        sc->ctrl.big_colors = 0;
+    }
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < kPresWords; i += gridDim.x * kBlock)
+        sc->pres[i] = 0u;
+}
+
+// Light rows, 8 lanes per vertex; heavy rows are left to the next kernel
+// (which finds them again by degree instead of through a list).
+__global__ void __launch_bounds__(kBlock) k_validate_na_light(ValArgs a) {
+    __shared__ uint32_t s_pres[kPresWords];
+    for (int i = threadIdx.x; i < kPresWords; i += kBlock) s_pres[i] = 0u;
+    __syncthreads();
+    const int gi = threadIdx.x / kValG, gl = threadIdx.x % kValG;
+    const int64_t groups = static_cast<int64_t>(gridDim.x) * (kBlock / kValG);
+    int32_t my_max = 0;
+    unsigned long long conf = 0, unc = 0;
+    const int64_t n_pad = (a.g.n + groups - 1) / groups * groups;
+    for (int64_t v = static_cast<int64_t>(blockIdx.x) * (kBlock / kValG) + gi; v < n_pad; v += groups) {
+        const bool valid = v < a.g.n;
+        int64_t beg = 0;
+        int32_t deg = 0, cv = 0;
+        bool heavy = false;
+        if (valid) {
+            row_of(a.g, static_cast<int32_t>(v), beg, deg, &a.c->err);
+            cv = a.colors[v];
+            heavy = deg > kHeavyDeg;
+        }
+        int32_t same = same_color<4>(a, beg, heavy ? 0 : deg, cv, gl, kValG);
+#pragma unroll
+        for (int d = kValG / 2; d >= 1; d >>= 1) same += __shfl_xor_sync(kFull, same, d);
+        if (valid && gl == 0 && !heavy) account(a, static_cast<int32_t>(v), cv, same, s_pres, conf, unc, my_max);
+    }
+    warp_add(&a.c->conflicts, conf);
+    warp_add(&a.c->uncolored, unc);
+    warp_max(&a.c->max_color, my_max);
+    flush_presence(a, s_pres);
+}
+
+// Heavy rows (degree > kHeavyDeg), one block per row, found by a scan of the
+// degrees.
+__global__ void __launch_bounds__(kBlock) k_validate_na_heavy(ValArgs a) {
+    __shared__ uint32_t s_pres[kPresWords];
+    __shared__ int32_t s_sum[kWarps];
+    for (int i = threadIdx.x; i < kPresWords; i += kBlock) s_pres[i] = 0u;
+    __syncthreads();
+    int32_t my_max = 0;
+    unsigned long long conf = 0, unc = 0;
+    for (int64_t v0 = static_cast<int64_t>(blockIdx.x) * kBlock; v0 < a.g.n;
+         v0 += static_cast<int64_t>(gridDim.x) * kBlock) {
+        // the block's threads look at kBlock vertices, then walk the heavy ones
+        const int64_t mine = v0 + threadIdx.x;
+        bool heavy = false;
+        if (mine < a.g.n) {
+            const int64_t b = a.g.off[mine], e = a.g.off[mine + 1];
+            heavy = e - b > kHeavyDeg;
+        }
+        uint32_t mask = __ballot_sync(kFull, heavy);
+        __shared__ uint32_t s_mask[kWarps];
+        if (lane_id() == 0) s_mask[threadIdx.x >> 5] = mask;
+        __syncthreads();
+        for (int w = 0; w < kWarps; ++w) {
+            uint32_t m = s_mask[w];
+            while (m) {
+                const int bit = __ffs(m) - 1;
+                m &= m - 1;
+                const int32_t v = static_cast<int32_t>(v0 + w * 32 + bit);
+                int64_t beg;
+                int32_t deg;
+                row_of(a.g, v, beg, deg, &a.c->err);
+                const int32_t cv = a.colors[v];
+                int32_t same = same_color<4>(a, beg, deg, cv, threadIdx.x, kBlock);
+#pragma unroll
+                for (int d = 16; d >= 1; d >>= 1) same += __shfl_xor_sync(kFull, same, d);
+                if (lane_id() == 0) s_sum[threadIdx.x >> 5] = same;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int32_t tot = 0;
+                    for (int q = 0; q < kWarps; ++q) tot += s_sum[q];
+                    account(a, v, cv, tot, s_pres, conf, unc, my_max);
+                }
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+    }
+    warp_add(&a.c->conflicts, conf);
+    warp_add(&a.c->uncolored, unc);
+    warp_max(&a.c->max_color, my_max);
+    flush_presence(a, s_pres);
+}
+
+namespace {
+constexpr int kNoAllocDevices = 64;
+std::mutex g_na_mu;
+NoAllocScratch* g_na_ptr[kNoAllocDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the array's name is only a host-side stand-in).
+gc_status noalloc_scratch(NoAllocScratch** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return GC_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocDevices) return GC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_validate_scratch);
+        if (e != cudaSuccess || !p) return GC_ERR_CUDA;
+        g_na_ptr[dev] = static_cast<NoAllocScratch*>(p);
+    }
+    *out = g_na_ptr[dev];
+    return GC_OK;
+}
+
+int noalloc_grid(const void* kernel) {
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return std::max(1, sms) * per_sm;
+}
+}  // namespace
+
+gc_status validate_noalloc_device(const Graph& g, const int32_t* colors, gc_validation* out,
+                                  cudaStream_t s) {
+    std::memset(out, 0, sizeof(*out));
+    out->first_bad_vertex = -1;
+    if (g.n == 0) return GC_OK;
+    NoAllocScratch* sc = nullptr;
+    gc_status st = noalloc_scratch(&sc);
+    if (st != GC_OK) return st;
+    ValArgs a{g, colors, &sc->ctrl, sc->pres, nullptr};
+    k_validate_na_clear<<<8, kBlock, 0, s>>>(sc);
+    k_validate_na_light<<<noalloc_grid(reinterpret_cast<const void*>(k_validate_na_light)), kBlock, 0, s>>>(a);
+    k_validate_na_heavy<<<noalloc_grid(reinterpret_cast<const void*>(k_validate_na_heavy)), kBlock, 0, s>>>(a);
+    k_count_bits<<<8, kBlock, 0, s>>>(kPresWords, sc->pres, &sc->ctrl);
+    note_launches(4);
+    ValCtrl h;
+    cudaError_t ce = cudaMemcpyAsync(&h, &sc->ctrl, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    if (h.err & kErrBadGraph) return GC_ERR_BAD_GRAPH;
+    if (h.big_colors > 0) return GC_ERR_INVALID_ARG;  // a color >= 65536: beyond the scratch
+    out->n_conflicts = static_cast<int64_t>(h.conflicts);
+    out->n_uncolored = static_cast<int64_t>(h.uncolored);
+    out->max_color = h.max_color;
+    out->n_distinct = static_cast<int32_t>(h.distinct);
     out->first_bad_vertex = h.first_bad == LLONG_MAX ? -1 : static_cast<int64_t>(h.first_bad);
     return GC_OK;
 }
