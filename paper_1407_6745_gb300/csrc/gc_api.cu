@@ -203,6 +203,7 @@ struct DeviceGraph {
         if (h->mem == GC_MEM_DEVICE) {
             g.off = h->offsets;
             g.idx = h->idx;
+            g.vec = (reinterpret_cast<uintptr_t>(g.idx) & 15u) == 0;
             return GC_OK;
         }
         if (!off.alloc((h->n + 1) * sizeof(int64_t), s) || !idx.alloc(h->nnz * sizeof(int32_t), s))
@@ -217,6 +218,7 @@ struct DeviceGraph {
                 return GC_ERR_CUDA;
         g.off = off.as<int64_t>();
         g.idx = idx.as<int32_t>();
+        g.vec = (reinterpret_cast<uintptr_t>(g.idx) & 15u) == 0;
         return GC_OK;
     }
 };
@@ -430,6 +432,7 @@ gc_status gc_validate_noalloc(const gc_graph* g, const int32_t* colors, gc_valid
     dg.nnz = g->nnz;
     dg.off = g->offsets;
     dg.idx = g->idx;
+    dg.vec = (reinterpret_cast<uintptr_t>(dg.idx) & 15u) == 0;
     return validate_noalloc_device(dg, colors, out, static_cast<cudaStream_t>(stream));
 }
 

@@ -229,32 +229,23 @@ __global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
 // Does some neighbor in this lane's stripe have v's tentative color and a
 // larger (priority, id)?  With equal tentative colors the 64-bit keys order
 // as the priorities; equal keys fall back to the id.  U gathers in flight.
-template <int U>
+template <int UC>
 __device__ __forceinline__ bool loses(const SpecArgs& a, const WorkItem& it, int32_t lane0,
                                       int32_t stride) {
     if (it.deg == 0) return false;
-    const uint64_t kv = __ldg(reinterpret_cast<const unsigned long long*>(a.key) + it.v);
+    const unsigned long long* key = reinterpret_cast<const unsigned long long*>(a.key);
+    const uint64_t kv = __ldg(key + it.v);
     const uint32_t tv = static_cast<uint32_t>(kv >> 32);
-    for (int32_t k0 = lane0; k0 < it.deg; k0 += stride * U) {
-        int32_t u[U];
-        uint64_t ku[U];
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const int32_t k = k0 + i * stride;
-            u[i] = k < it.deg ? load_nbr(a.g, it.beg + k, &a.ctrl->err) : -1;
-        }
-#pragma unroll
-        for (int i = 0; i < U; ++i)
-            ku[i] = __ldg(reinterpret_cast<const unsigned long long*>(a.key) + (u[i] >= 0 ? u[i] : 0));
-        bool lose = false;
-#pragma unroll
-        for (int i = 0; i < U; ++i)
-            if (u[i] >= 0 && u[i] != it.v && static_cast<uint32_t>(ku[i] >> 32) == tv &&
-                (ku[i] > kv || (ku[i] == kv && u[i] > it.v)))
+    bool lose = false;
+    for_each_nbr<UC, uint64_t>(
+        a.g, it.beg, it.deg, lane0, stride, [&](int32_t u) { return __ldg(key + u); },
+        [&](int32_t u, uint64_t ku) {
+            if (u != it.v && static_cast<uint32_t>(ku >> 32) == tv &&
+                (ku > kv || (ku == kv && u > it.v)))
                 lose = true;
-        if (lose) return true;
-    }
-    return false;
+        },
+        &a.ctrl->err);
+    return lose;
 }
 
 template <int G>
@@ -296,7 +287,7 @@ __global__ void __launch_bounds__(kBlock) k_conflict(SpecArgs a) {
         switch (b) {
         case 0: {
             const WorkItem it = load_item(list + rt.start[0] + first);
-            const bool lose = __syncthreads_or(loses<4>(a, it, threadIdx.x, kBlock));
+            const bool lose = __syncthreads_or(loses<1>(a, it, threadIdx.x, kBlock));
             if (threadIdx.x == 0) {
                 edges += static_cast<unsigned long long>(it.deg);
                 if (lose) {

@@ -62,6 +62,7 @@ struct Graph {
     const int32_t* idx;
     int32_t n;
     int64_t nnz;
+    int32_t vec;  // idx is 16-byte aligned: rows are read as aligned 4-id chunks
 };
 
 // ---------------------------------------------------------------------------
@@ -182,8 +183,33 @@ __device__ __forceinline__ void row_range(const Graph& g, int32_t v, int64_t& be
     }
 }
 
+// Streamed data (adjacency, work items) is read once per pass: it is loaded
+// with an L2 evict-first policy and without L1 allocation, so it does not
+// push the gathered color arrays out of L2.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ int32_t ld_stream(const int32_t* ptr) {
+    int32_t x;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;"
+        : "=r"(x)
+        : "l"(ptr), "l"(policy_evict_first()));
+    return x;
+}
+
+__device__ __forceinline__ int4 ld_stream4(const void* ptr) {
+    int4 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.b32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(ptr), "l"(policy_evict_first()));
+    return r;
+}
+
 __device__ __forceinline__ int32_t load_nbr(const Graph& g, int64_t e, uint32_t* err) {
-    const int32_t u = __ldg(g.idx + e);
+    const int32_t u = ld_stream(g.idx + e);
     if (static_cast<uint32_t>(u) >= static_cast<uint32_t>(g.n)) {
         atomicOr(err, kErrBadGraph);
         return -1;
@@ -202,7 +228,7 @@ struct __align__(16) WorkItem {
 };
 
 __device__ __forceinline__ WorkItem load_item(const WorkItem* p) {
-    const int4 r = __ldcg(reinterpret_cast<const int4*>(p));
+    const int4 r = ld_stream4(p);
     WorkItem w;
     w.beg = (static_cast<int64_t>(static_cast<uint32_t>(r.y)) << 32) | static_cast<uint32_t>(r.x);
     w.v = r.z;
@@ -240,24 +266,88 @@ __device__ __forceinline__ void row_of(const Graph& g, int32_t v, int64_t& beg, 
 // turns the loaded word into a color, or a value < 1 to ignore the neighbor.
 // Each lane takes the neighbors lane0, lane0 + stride, ...; U per batch.
 // ---------------------------------------------------------------------------
-template <int U, class Fetch, class Mark>
+// Visits the neighbors of a row, lane `lane0` of a group of `stride` lanes
+// taking every stride-th piece.  load(u) issues the gather for neighbor u
+// (called for a whole batch before any visit, so the batch's gathers are in
+// flight together); visit(u, x) consumes it.  With an aligned idx the row is
+// read as aligned 16-byte chunks of 4 ids (UC chunks per lane per batch),
+// the entries outside the row masked off; otherwise 4 * UC single ids.
+template <int UC, class T, class Load, class Visit>
+__device__ __forceinline__ void for_each_nbr(const Graph& g, int64_t beg, int32_t deg,
+                                             int32_t lane0, int32_t stride, Load&& load,
+                                             Visit&& visit, uint32_t* err) {
+    constexpr int U = 4 * UC;
+    if (deg <= 0) return;
+    if (g.vec) {
+        const int64_t a0 = beg & ~static_cast<int64_t>(3);
+        const int64_t end = beg + deg;
+        const int32_t nch = static_cast<int32_t>((end - a0 + 3) >> 2);
+        for (int32_t c0 = lane0; c0 < nch; c0 += stride * UC) {
+            int32_t u[U];
+#pragma unroll
+            for (int i = 0; i < UC; ++i) {
+                const int32_t c = c0 + i * stride;
+                const int64_t e0 = a0 + 4 * static_cast<int64_t>(c);
+                int4 q = make_int4(-1, -1, -1, -1);
+                if (c < nch) {
+                    if (e0 + 4 <= g.nnz) {
+                        q = ld_stream4(g.idx + e0);
+                    } else {  // the last ids of the array: no read past its end
+                        q.x = e0 < g.nnz ? ld_stream(g.idx + e0) : -1;
+                        q.y = e0 + 1 < g.nnz ? ld_stream(g.idx + e0 + 1) : -1;
+                        q.z = e0 + 2 < g.nnz ? ld_stream(g.idx + e0 + 2) : -1;
+                        q.w = e0 + 3 < g.nnz ? ld_stream(g.idx + e0 + 3) : -1;
+                    }
+                }
+                const int32_t qq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t e = e0 + j;
+                    int32_t v = -1;
+                    if (c < nch && e >= beg && e < end) {
+                        v = qq[j];
+                        if (static_cast<uint32_t>(v) >= static_cast<uint32_t>(g.n)) {
+                            atomicOr(err, kErrBadGraph);
+                            v = -1;
+                        }
+                    }
+                    u[4 * i + j] = v;
+                }
+            }
+            T x[U];
+#pragma unroll
+            for (int i = 0; i < U; ++i) x[i] = load(u[i] >= 0 ? u[i] : 0);
+#pragma unroll
+            for (int i = 0; i < U; ++i)
+                if (u[i] >= 0) visit(u[i], x[i]);
+        }
+    } else {
+        for (int32_t k0 = lane0; k0 < deg; k0 += stride * U) {
+            int32_t u[U];
+#pragma unroll
+            for (int i = 0; i < U; ++i) {
+                const int32_t k = k0 + i * stride;
+                u[i] = k < deg ? load_nbr(g, beg + k, err) : -1;
+            }
+            T x[U];
+#pragma unroll
+            for (int i = 0; i < U; ++i) x[i] = load(u[i] >= 0 ? u[i] : 0);
+#pragma unroll
+            for (int i = 0; i < U; ++i)
+                if (u[i] >= 0) visit(u[i], x[i]);
+        }
+    }
+}
+
+// Colors of the neighbors through a Fetch: raw(u) issues the load (no
+// branch), resolve(u, x) turns it into a color, or a value < 1 to ignore.
+template <int UC, class Fetch, class Mark>
 __device__ __forceinline__ void scan_row(const Graph& g, int64_t beg, int32_t deg, int32_t lane0,
                                          int32_t stride, const Fetch& fetch, Mark&& mark,
                                          uint32_t* err) {
-    for (int32_t k0 = lane0; k0 < deg; k0 += stride * U) {
-        int32_t u[U];
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const int32_t k = k0 + i * stride;
-            u[i] = k < deg ? load_nbr(g, beg + k, err) : -1;
-        }
-        int32_t x[U];
-#pragma unroll
-        for (int i = 0; i < U; ++i) x[i] = fetch.raw(u[i] >= 0 ? u[i] : 0);
-#pragma unroll
-        for (int i = 0; i < U; ++i)
-            if (u[i] >= 0) mark(fetch.resolve(u[i], x[i]));
-    }
+    for_each_nbr<UC, int32_t>(
+        g, beg, deg, lane0, stride, [&](int32_t u) { return fetch.raw(u); },
+        [&](int32_t u, int32_t x) { mark(fetch.resolve(u, x)); }, err);
 }
 
 // Register path, G lanes per vertex; requires deg + j < 64.  All 32 lanes of
@@ -289,7 +379,7 @@ __device__ __forceinline__ int32_t choose_warp(const Graph& g, int64_t beg, int3
         bm[l] = 0u;
         bm[l + 32] = 0u;
         __syncwarp();
-        scan_row<U>(g, beg, deg, l, 32, fetch,
+        scan_row<1>(g, beg, deg, l, 32, fetch,
                     [&](int32_t c) {
                         const uint32_t d = static_cast<uint32_t>(c - base);
                         if (c > 0 && d < 32u * kWarpBitmapWords) atomicOr(&bm[d >> 5], 1u << (d & 31));
@@ -339,7 +429,7 @@ __device__ __forceinline__ int32_t choose_block(const Graph& g, int64_t beg, int
     for (;;) {
         for (int i = t; i < kBlockBitmapWords; i += kBlock) s.bm[i] = 0u;
         __syncthreads();
-        scan_row<U>(g, beg, deg, t, kBlock, fetch,
+        scan_row<1>(g, beg, deg, t, kBlock, fetch,
                     [&](int32_t c) {
                         const uint32_t d = static_cast<uint32_t>(c - base);
                         if (c > 0 && d < 32u * kBlockBitmapWords) atomicOr(&s.bm[d >> 5], 1u << (d & 31));
@@ -384,8 +474,8 @@ __device__ __forceinline__ int32_t choose_block(const Graph& g, int64_t beg, int
     }
 }
 
-// Neighbor-loads per lane in flight, per bucket (group of 32/16/8/4 lanes).
-template <int G> struct LanesUnroll { static constexpr int U = G == 32 ? 2 : G == 16 ? 4 : 8; };
+// 4-id pieces per lane per batch, per group size (32/16/8/4 lanes).
+template <int G> struct LanesUnroll { static constexpr int U = G == 4 ? 2 : 1; };
 
 // ---------------------------------------------------------------------------
 // Tiles: a list is cut into segments (one bucket each); segment s holds

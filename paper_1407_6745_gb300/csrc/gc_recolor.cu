@@ -492,7 +492,7 @@ __device__ __forceinline__ void recolor_chunk(const RcArgs& a, const RecolorFetc
         bm[l + 32] = 0u;
         __syncwarp();
         const int32_t base = w0 * 32 + 1;
-        scan_row<4>(a.g, it.beg, it.deg, l, 32, f,
+        scan_row<2>(a.g, it.beg, it.deg, l, 32, f,
                     [&](int32_t c) {
                         const uint32_t d = static_cast<uint32_t>(c - base);
                         if (c > 0 && d < 32u * kWarpBitmapWords) atomicOr(&bm[d >> 5], 1u << (d & 31));

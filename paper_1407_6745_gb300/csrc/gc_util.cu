@@ -34,23 +34,14 @@ struct ValArgs {
     int32_t* heavy;    // n
 };
 
-// Count of neighbors with v's color in this lane's stripe, U loads in flight.
-template <int U>
+// Count of neighbors with v's color in this lane's stripe.
+template <int UC>
 __device__ __forceinline__ int32_t same_color(const ValArgs& a, int64_t beg, int32_t deg, int32_t cv,
                                               int32_t lane0, int32_t stride) {
     int32_t cnt = 0;
-    for (int32_t k0 = lane0; k0 < deg; k0 += stride * U) {
-        int32_t u[U], x[U];
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const int32_t k = k0 + i * stride;
-            u[i] = k < deg ? load_nbr(a.g, beg + k, &a.c->err) : -1;
-        }
-#pragma unroll
-        for (int i = 0; i < U; ++i) x[i] = __ldg(a.colors + (u[i] >= 0 ? u[i] : 0));
-#pragma unroll
-        for (int i = 0; i < U; ++i) cnt += (u[i] >= 0 && x[i] == cv);
-    }
+    for_each_nbr<UC, int32_t>(
+        a.g, beg, deg, lane0, stride, [&](int32_t u) { return __ldg(a.colors + u); },
+        [&](int32_t, int32_t x) { cnt += x == cv; }, &a.c->err);
     return cnt;
 }
 
@@ -91,7 +82,7 @@ __global__ void __launch_bounds__(kBlock) k_validate(ValArgs a) {
             cv = a.colors[v];
             heavy = deg > kHeavyDeg;
         }
-        int32_t same = same_color<4>(a, beg, heavy ? 0 : deg, cv, gl, kValG);
+        int32_t same = same_color<1>(a, beg, heavy ? 0 : deg, cv, gl, kValG);
 #pragma unroll
         for (int d = kValG / 2; d >= 1; d >>= 1) same += __shfl_xor_sync(kFull, same, d);
         if (valid && gl == 0) {
@@ -120,7 +111,7 @@ __global__ void __launch_bounds__(kBlock) k_validate_heavy(ValArgs a) {
         int32_t deg;
         row_of(a.g, v, beg, deg, &a.c->err);
         const int32_t cv = a.colors[v];
-        int32_t same = same_color<4>(a, beg, deg, cv, threadIdx.x, kBlock);
+        int32_t same = same_color<1>(a, beg, deg, cv, threadIdx.x, kBlock);
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) same += __shfl_xor_sync(kFull, same, d);
         if (lane_id() == 0) s_sum[threadIdx.x >> 5] = same;
@@ -263,7 +254,7 @@ __global__ void __launch_bounds__(kBlock) k_validate_na_light(ValArgs a) {
             cv = a.colors[v];
             heavy = deg > kHeavyDeg;
         }
-        int32_t same = same_color<4>(a, beg, heavy ? 0 : deg, cv, gl, kValG);
+        int32_t same = same_color<1>(a, beg, heavy ? 0 : deg, cv, gl, kValG);
 #pragma unroll
         for (int d = kValG / 2; d >= 1; d >>= 1) same += __shfl_xor_sync(kFull, same, d);
         if (valid && gl == 0 && !heavy) account(a, static_cast<int32_t>(v), cv, same, s_pres, conf, unc, my_max);
@@ -306,7 +297,7 @@ __global__ void __launch_bounds__(kBlock) k_validate_na_heavy(ValArgs a) {
                 int32_t deg;
                 row_of(a.g, v, beg, deg, &a.c->err);
                 const int32_t cv = a.colors[v];
-                int32_t same = same_color<4>(a, beg, deg, cv, threadIdx.x, kBlock);
+                int32_t same = same_color<1>(a, beg, deg, cv, threadIdx.x, kBlock);
 #pragma unroll
                 for (int d = 16; d >= 1; d >>= 1) same += __shfl_xor_sync(kFull, same, d);
                 if (lane_id() == 0) s_sum[threadIdx.x >> 5] = same;
