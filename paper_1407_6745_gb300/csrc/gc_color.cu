@@ -237,7 +237,7 @@ __device__ __forceinline__ bool loses(const SpecArgs& a, const WorkItem& it, int
     const uint64_t kv = __ldg(key + it.v);
     const uint32_t tv = static_cast<uint32_t>(kv >> 32);
     bool lose = false;
-    for_each_nbr<UC, uint64_t>(
+    for_each_nbr<UC, uint64_t, true>(
         a.g, it.beg, it.deg, lane0, stride, [&](int32_t u) { return __ldg(key + u); },
         [&](int32_t u, uint64_t ku) {
             if (u != it.v && static_cast<uint32_t>(ku >> 32) == tv &&

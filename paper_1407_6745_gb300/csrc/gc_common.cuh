@@ -267,18 +267,20 @@ __device__ __forceinline__ void row_of(const Graph& g, int32_t v, int64_t& beg, 
 // Each lane takes the neighbors lane0, lane0 + stride, ...; U per batch.
 // ---------------------------------------------------------------------------
 // Visits the neighbors of a row, lane `lane0` of a group of `stride` lanes
-// taking every stride-th piece.  load(u) issues the gather for neighbor u
+// taking every stride-th piece.  (kVec selects the chunked reads; color
+// selection keeps single-id reads, measured faster there: the chunked form
+// holds more registers per gather batch.)  load(u) issues the gather for neighbor u
 // (called for a whole batch before any visit, so the batch's gathers are in
 // flight together); visit(u, x) consumes it.  With an aligned idx the row is
 // read as aligned 16-byte chunks of 4 ids (UC chunks per lane per batch),
 // the entries outside the row masked off; otherwise 4 * UC single ids.
-template <int UC, class T, class Load, class Visit>
+template <int UC, class T, bool kVec, class Load, class Visit>
 __device__ __forceinline__ void for_each_nbr(const Graph& g, int64_t beg, int32_t deg,
                                              int32_t lane0, int32_t stride, Load&& load,
                                              Visit&& visit, uint32_t* err) {
     constexpr int U = 4 * UC;
     if (deg <= 0) return;
-    if (g.vec) {
+    if (kVec && g.vec) {
         const int64_t a0 = beg & ~static_cast<int64_t>(3);
         const int64_t end = beg + deg;
         const int32_t nch = static_cast<int32_t>((end - a0 + 3) >> 2);
@@ -345,7 +347,7 @@ template <int UC, class Fetch, class Mark>
 __device__ __forceinline__ void scan_row(const Graph& g, int64_t beg, int32_t deg, int32_t lane0,
                                          int32_t stride, const Fetch& fetch, Mark&& mark,
                                          uint32_t* err) {
-    for_each_nbr<UC, int32_t>(
+    for_each_nbr<UC, int32_t, false>(
         g, beg, deg, lane0, stride, [&](int32_t u) { return fetch.raw(u); },
         [&](int32_t u, int32_t x) { mark(fetch.resolve(u, x)); }, err);
 }

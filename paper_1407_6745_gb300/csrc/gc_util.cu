@@ -39,7 +39,7 @@ template <int UC>
 __device__ __forceinline__ int32_t same_color(const ValArgs& a, int64_t beg, int32_t deg, int32_t cv,
                                               int32_t lane0, int32_t stride) {
     int32_t cnt = 0;
-    for_each_nbr<UC, int32_t>(
+    for_each_nbr<UC, int32_t, true>(
         a.g, beg, deg, lane0, stride, [&](int32_t u) { return __ldg(a.colors + u); },
         [&](int32_t, int32_t x) { cnt += x == cv; }, &a.c->err);
     return cnt;
