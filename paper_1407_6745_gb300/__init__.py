@@ -70,7 +70,7 @@ class _KernelTime(ctypes.Structure):
 class _Tuning(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in ("g4_max_deg", "g8_max_deg", "g16_max_deg",
                                                "warp_max_deg", "grid_blocks", "recolor_mode",
-                                               "spin_limit", "reserved")]
+                                               "spin_limit", "spec_graph")]
 
 
 def library_path() -> str:
@@ -293,7 +293,7 @@ def gc_get_tuning():
     lib = load()
     t = _Tuning()
     _check(lib.gc_get_tuning(ctypes.byref(t)), "gc_get_tuning")
-    return {k: getattr(t, k) for k, _ in _Tuning._fields_ if k != "reserved"}
+    return {k: getattr(t, k) for k, _ in _Tuning._fields_}
 
 
 def gc_profile_enable(on: bool = True):

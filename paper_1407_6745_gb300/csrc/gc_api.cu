@@ -52,7 +52,7 @@ Tuning default_tuning() {
     t.grid_blocks = 0;
     t.recolor_mode = 0;
     t.spin_limit = 1 << 20;
-    t.reserved = 0;
+    t.spec_graph = 1;
     return t;
 }
 Tuning g_tune = default_tuning();
@@ -179,6 +179,7 @@ gc_status status_from_err_bits(uint32_t bits) {
     if (bits & kErrBadGraph) return GC_ERR_BAD_GRAPH;
     if (bits & kErrImproper) return GC_ERR_IMPROPER_INPUT;
     if (bits & kErrTimeout) return GC_ERR_TIMEOUT;
+    if (bits & kErrRoundLimit) return GC_ERR_ROUND_LIMIT;
     return GC_OK;
 }
 
@@ -441,7 +442,7 @@ gc_status gc_set_tuning(const gc_tuning* t) {
     if (t) {
         if (t->g4_max_deg < 0 || t->g8_max_deg < t->g4_max_deg || t->g16_max_deg < t->g8_max_deg ||
             t->warp_max_deg < 0 || t->grid_blocks < 0 || t->recolor_mode < 0 ||
-            t->recolor_mode > 1 || t->spin_limit < 1)
+            t->recolor_mode > 1 || t->spin_limit < 1 || t->spec_graph < 0 || t->spec_graph > 1)
             return GC_ERR_INVALID_ARG;
         v.g4_max_deg = t->g4_max_deg;
         v.g8_max_deg = t->g8_max_deg;
@@ -450,6 +451,7 @@ gc_status gc_set_tuning(const gc_tuning* t) {
         v.grid_blocks = t->grid_blocks;
         v.recolor_mode = t->recolor_mode;
         v.spin_limit = t->spin_limit;
+        v.spec_graph = t->spec_graph;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune = v;
@@ -466,7 +468,7 @@ gc_status gc_get_tuning(gc_tuning* out) {
     out->grid_blocks = t.grid_blocks;
     out->recolor_mode = t.recolor_mode;
     out->spin_limit = t.spin_limit;
-    out->reserved = 0;
+    out->spec_graph = t.spec_graph;
     return GC_OK;
 }
 

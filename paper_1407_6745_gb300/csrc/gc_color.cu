@@ -51,6 +51,9 @@ struct SpecArgs {
     WorkItem* list0;   // work lists (ping-pong), bucket regions
     WorkItem* list1;
     SpecCtrl* ctrl;
+    unsigned long long cond;  // WHILE-node handle (graph mode)
+    int32_t use_cond;
+    int32_t round_limit;
 };
 
 // ---------------------------------------------------------------------------
@@ -325,6 +328,9 @@ __global__ void __launch_bounds__(kBlock) k_conflict(SpecArgs a) {
         c->conflicts += static_cast<unsigned long long>(total);
         c->round = round + 1;
         c->done_blocks = 0u;
+        const bool over = total > 0 && round + 1 >= a.round_limit;
+        if (over) c->err |= kErrRoundLimit;
+        if (a.use_cond) cudaGraphSetConditional(a.cond, (total > 0 && !over) ? 1u : 0u);
     }
 }
 
@@ -352,6 +358,55 @@ struct PinnedWord {
 };
 thread_local PinnedWord t_pinned;
 }  // namespace
+
+// The rounds as one CUDA graph: a WHILE node whose body is {tentative,
+// conflict}; the last block of the conflict kernel sets the condition from
+// the size of the next work set, so no round waits for the host.
+gc_status rounds_in_graph(SpecArgs& a, int32_t X, int grid_t, int grid_c, cudaStream_t s) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    cudaGraphConditionalHandle handle = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    alignas(cudaGraphNodeParams) unsigned char cp_buf[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_buf, 0, sizeof(cp_buf));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_buf);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp);
+    SpecArgs ga = a;
+    ga.cond = handle;
+    ga.use_cond = 1;
+    void* args[] = {&ga};
+    cudaGraphNode_t n1 = nullptr, n2 = nullptr;
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaKernelNodeParams k1;
+        std::memset(&k1, 0, sizeof(k1));
+        k1.func = X > 1 ? reinterpret_cast<void*>(k_tentative<true>) : reinterpret_cast<void*>(k_tentative<false>);
+        k1.gridDim = dim3(grid_t);
+        k1.blockDim = dim3(kBlock);
+        k1.kernelParams = args;
+        cudaKernelNodeParams k2 = k1;
+        k2.func = reinterpret_cast<void*>(k_conflict);
+        k2.gridDim = dim3(grid_c);
+        e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &k1);
+        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &k2);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) {
+        prof_begin(KID_SPEC_GRAPH, s);
+        e = cudaGraphLaunch(exec, s);
+        prof_end(KID_SPEC_GRAPH, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_status(e);
+}
 
 gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors_out,
                        gc_stats* stats, cudaStream_t s) {
@@ -390,17 +445,22 @@ gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors
     GC_LAUNCH(KID_SPEC_SETUP, s, k_spec_setup<<<setup_grid, kBlock, 0, s>>>(a));
     GC_LAUNCH(KID_SPEC_FILL, s, k_spec_fill<<<setup_grid, kBlock, 0, s>>>(a));
     gc_status st = GC_OK;
-    int32_t rounds = 0;
-    for (;;) {
-        if (X > 1) GC_LAUNCH(KID_TENTATIVE, s, k_tentative<true><<<grid_t, kBlock, 0, s>>>(a));
-        else GC_LAUNCH(KID_TENTATIVE, s, k_tentative<false><<<grid_t, kBlock, 0, s>>>(a));
-        GC_LAUNCH(KID_CONFLICT, s, k_conflict<<<grid_c, kBlock, 0, s>>>(a));
-        ++rounds;
-        cudaMemcpyAsync(t_pinned.p, &a.ctrl->active, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-        cudaError_t ce = cudaStreamSynchronize(s);
-        if (ce != cudaSuccess) { st = cuda_status(ce); break; }
-        if (t_pinned.p[0] == 0) break;
-        if (rounds > n + 1) { st = GC_ERR_ROUND_LIMIT; break; }
+    a.round_limit = static_cast<int32_t>(std::min<int64_t>(n + 2, INT32_MAX));
+    if (a.tune.spec_graph) {
+        st = rounds_in_graph(a, X, grid_t, grid_c, s);
+    } else {
+        int32_t rounds = 0;
+        for (;;) {
+            if (X > 1) GC_LAUNCH(KID_TENTATIVE, s, k_tentative<true><<<grid_t, kBlock, 0, s>>>(a));
+            else GC_LAUNCH(KID_TENTATIVE, s, k_tentative<false><<<grid_t, kBlock, 0, s>>>(a));
+            GC_LAUNCH(KID_CONFLICT, s, k_conflict<<<grid_c, kBlock, 0, s>>>(a));
+            ++rounds;
+            cudaMemcpyAsync(t_pinned.p, &a.ctrl->active, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            cudaError_t ce = cudaStreamSynchronize(s);
+            if (ce != cudaSuccess) { st = cuda_status(ce); break; }
+            if (t_pinned.p[0] == 0) break;
+            if (rounds >= a.round_limit) { st = GC_ERR_ROUND_LIMIT; break; }
+        }
     }
     cudaEventRecord(e1, s);
     SpecCtrl h;
@@ -408,6 +468,7 @@ gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess && st == GC_OK) st = cuda_status(ce);
     if (st == GC_OK) st = status_from_err_bits(h.err);
+    if (a.tune.spec_graph) note_launches(2 * static_cast<int64_t>(h.round));
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->rounds = h.round;

@@ -34,6 +34,7 @@ constexpr int kBlockBitmapWords = 4096; // 131072 colors per window, per block
 constexpr uint32_t kErrBadGraph = 1u;
 constexpr uint32_t kErrTimeout = 2u;
 constexpr uint32_t kErrImproper = 4u;
+constexpr uint32_t kErrRoundLimit = 8u;
 
 // Scheduling thresholds (runtime; tuned per workload).
 struct Tuning {
@@ -44,7 +45,7 @@ struct Tuning {
     int32_t grid_blocks;   // persistent grid size (0 = 8 per SM)
     int32_t recolor_mode;  // 0 = dataflow (one launch), 1 = one launch per class
     int32_t spin_limit;    // bounded wait iterations in the dataflow recolor
-    int32_t reserved;
+    int32_t spec_graph;    // 1: speculative rounds in a CUDA graph WHILE node; 0: host loop
 };
 
 __host__ __device__ inline int bucket_of(int64_t deg, int32_t X, const Tuning& t) {

@@ -40,7 +40,7 @@ enum KernelId {
     KID_SPEC_SETUP, KID_SPEC_FILL, KID_TENTATIVE, KID_CONFLICT, KID_PRIORITIES,
     KID_RC_BUCKET, KID_RC_VALIDATE, KID_RC_HIST, KID_RC_ORDER, KID_RC_SCATTER,
     KID_RC_RECOLOR, KID_RC_STEP, KID_VALIDATE, KID_VALIDATE_HEAVY, KID_MARK_PRESENT,
-    KID_COUNT_BITS, KID_CHECK_GRAPH, KID_COUNT_
+    KID_COUNT_BITS, KID_CHECK_GRAPH, KID_SPEC_GRAPH, KID_COUNT_
 };
 void prof_begin(KernelId k, cudaStream_t s);
 void prof_end(KernelId k, cudaStream_t s);

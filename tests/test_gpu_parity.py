@@ -148,6 +148,8 @@ def test_complete_graph_crosses_register_window():
     dict(warp_max_deg=1 << 30),
     dict(grid_blocks=7),
     dict(grid_blocks=1, recolor_mode=1),
+    dict(spec_graph=0),
+    dict(spec_graph=0, grid_blocks=3, recolor_mode=1),
 ])
 def test_results_do_not_depend_on_scheduling(knobs):
     g = gg.hubs(THRESHOLD_DEGREES[:-1], 6000, seed=8)
