@@ -422,6 +422,7 @@ gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors
         !sc_bucket.alloc(n, s) || !sc_ctrl.alloc(sizeof(SpecCtrl), s))
         return GC_ERR_OOM;
     SpecArgs a;
+    std::memset(&a, 0, sizeof(a));  // use_cond = 0: no WHILE node unless rounds_in_graph sets it
     a.g = g;
     a.X = X;
     a.seed = seed;
