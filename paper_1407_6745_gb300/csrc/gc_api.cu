@@ -110,11 +110,13 @@ void note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxe
 // Kernel timing
 // ---------------------------------------------------------------------------
 namespace {
-const char* const kKernelNames[KID_COUNT_] = {
+const char* const kKernelNames[] = {
     "k_spec_setup", "k_spec_fill", "k_tentative", "k_conflict", "k_priorities",
     "k_rc_bucket", "k_rc_validate", "k_rc_hist", "k_rc_order", "k_rc_scatter",
     "k_rc_recolor_coop", "k_rc_recolor_step", "k_validate", "k_validate_heavy",
-    "k_mark_present", "k_count_bits", "k_check_graph"};
+    "k_mark_present", "k_count_bits", "k_check_graph", "spec_rounds_graph"};
+static_assert(sizeof(kKernelNames) / sizeof(kKernelNames[0]) == KID_COUNT_,
+              "one name per KernelId");
 std::atomic<bool> g_prof_on{false};
 std::mutex g_prof_mu;
 long long g_prof_launches[KID_COUNT_];
