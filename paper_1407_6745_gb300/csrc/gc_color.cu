@@ -50,6 +50,9 @@ struct SpecCtrl {
     int32_t hub_next;       // slot bump (fill)
     unsigned long long hub_words;       // bitmap words needed (set-up)
     unsigned long long hub_words_used;  // bitmap bump (fill)
+    int32_t bad_where;                  // first failed internal check: site and index
+    int32_t pad2;
+    long long bad_index;
 };
 
 constexpr int32_t kSpecChunk = 1024;  // neighbors per chunk of a hub row
@@ -84,7 +87,20 @@ struct SpecArgs {
     int32_t* hub_done;
     int32_t* hub_lose;
     uint32_t* hub_bm;
+    int32_t n_hubs;           // slots allocated
+    int64_t hub_words_total;  // bitmap words allocated
+    int64_t list_len;         // entries of each work list
 };
+
+// Internal index checks: a failed one records where, skips the access and
+// makes the call return GC_ERR_CUDA-free GC_ERR_BAD_GRAPH-like status.
+__device__ __forceinline__ bool check_index(const SpecArgs& a, bool ok, int where, long long idx) {
+    if (ok) return true;
+    if (atomicOr(&a.ctrl->err, kErrInternal) == 0u || true) {
+        if (atomicCAS(&a.ctrl->bad_where, 0, where) == 0) a.ctrl->bad_index = idx;
+    }
+    return false;
+}
 
 // ---------------------------------------------------------------------------
 // Set-up: priorities, bucket sizes, then the round-0 work list (all vertices)
@@ -140,6 +156,7 @@ __global__ void __launch_bounds__(kBlock) k_spec_fill(SpecArgs a) {
         if (b == 0) {
             const int32_t slot = atomicAdd(&a.ctrl->hub_next, 1);
             const int32_t nch = spec_chunks(deg);
+            if (!check_index(a, slot < a.n_hubs, 1, slot)) continue;
             a.hub_v[slot] = v;
             a.hub_beg[slot] = beg;
             a.hub_deg[slot] = deg;
@@ -149,6 +166,12 @@ __global__ void __launch_bounds__(kBlock) k_spec_fill(SpecArgs a) {
             a.hub_done[slot] = 0;
             a.hub_lose[slot] = 0;
             const int32_t pos = atomicAdd(&a.ctrl->cnt[0][0], nch);
+            if (!check_index(a, a.hub_off[slot] + hub_bitmap_words(deg, a.X) <= a.hub_words_total, 2,
+                             a.hub_off[slot]))
+                continue;
+            if (!check_index(a, pos + nch <= a.ctrl->init_cnt[0] &&
+                                    s_start[0] + static_cast<int64_t>(pos) + nch <= a.list_len, 3, pos))
+                continue;
             for (int32_t c = 0; c < nch; ++c)
                 store_item(a.list0 + s_start[0] + pos + c, beg + static_cast<int64_t>(c) * kSpecChunk,
                            -(slot + 1), min(kSpecChunk, deg - c * kSpecChunk));
@@ -160,7 +183,8 @@ __global__ void __launch_bounds__(kBlock) k_spec_fill(SpecArgs a) {
             int32_t base = 0;
             if (lane_id() == leader) base = atomicAdd(&a.ctrl->cnt[0][b], __popc(peers));
             base = __shfl_sync(peers, base, leader);
-            store_item(a.list0 + s_start[b] + base + __popc(peers & ((1u << lane_id()) - 1u)), beg, v, deg);
+            const int64_t at = s_start[b] + static_cast<int64_t>(base) + __popc(peers & ((1u << lane_id()) - 1u));
+            if (check_index(a, at < a.list_len, 4, at)) store_item(a.list0 + at, beg, v, deg);
         }
     }
 }
@@ -271,8 +295,18 @@ __device__ __forceinline__ void tentative_chunk(const SpecArgs& a, const WorkIte
                                                 BlockScratch& s, unsigned long long& edges) {
     const int t = threadIdx.x;
     const int32_t slot = -it.v - 1;
+    // a bad slot or bitmap range is recorded and the chunk skipped (uniform)
+    if (!(slot >= 0 && slot < a.n_hubs)) {
+        if (t == 0) check_index(a, false, 5, slot);
+        return;
+    }
     const int32_t v = a.hub_v[slot];
     const int64_t words = hub_bitmap_words(a.hub_deg[slot], a.X);
+    if (!(a.hub_off[slot] >= 0 && a.hub_off[slot] + words <= a.hub_words_total &&
+          static_cast<uint32_t>(v) < static_cast<uint32_t>(a.g.n))) {
+        if (t == 0) check_index(a, false, 6, a.hub_off[slot]);
+        return;
+    }
     uint32_t* bm = a.hub_bm + a.hub_off[slot];
     const SnapshotFetch fetch{a.color};
     for (int64_t w0 = 0; w0 < words; w0 += kBlockBitmapWords) {
@@ -387,6 +421,10 @@ __device__ __forceinline__ void conflict_chunk(const SpecArgs& a, const WorkItem
                                                unsigned long long& edges, int32_t* s_flag) {
     const int t = threadIdx.x;
     const int32_t slot = -it.v - 1;
+    if (!(slot >= 0 && slot < a.n_hubs) || static_cast<uint32_t>(a.hub_v[slot]) >= static_cast<uint32_t>(a.g.n)) {
+        if (t == 0) check_index(a, false, 7, slot);
+        return;
+    }
     const int32_t v = a.hub_v[slot];
     const bool lose = __syncthreads_or(loses_v<1>(a, v, it.beg, it.deg, t, kBlock));
     if (t == 0) {
@@ -406,7 +444,8 @@ __device__ __forceinline__ void conflict_chunk(const SpecArgs& a, const WorkItem
     if (lost) {
         const int64_t words = hub_bitmap_words(a.hub_deg[slot], a.X);
         uint32_t* bm = a.hub_bm + a.hub_off[slot];
-        for (int64_t i = t; i < words; i += kBlock) bm[i] = 0u;
+        if (a.hub_off[slot] >= 0 && a.hub_off[slot] + words <= a.hub_words_total)
+            for (int64_t i = t; i < words; i += kBlock) bm[i] = 0u;
         if (t == 0) {
             a.hub_lose[slot] = 0;
             a.hub_done[slot] = 0;
@@ -416,9 +455,13 @@ __device__ __forceinline__ void conflict_chunk(const SpecArgs& a, const WorkItem
         __syncthreads();
         const int64_t beg = a.hub_beg[slot];
         const int32_t deg = a.hub_deg[slot];
-        for (int32_t c = t; c < nch; c += kBlock)
-            store_item(next + start0 + s_flag[1] + c, beg + static_cast<int64_t>(c) * kSpecChunk,
-                       -(slot + 1), min(kSpecChunk, deg - c * kSpecChunk));
+        const bool fits = s_flag[1] + nch <= a.ctrl->init_cnt[0] &&
+                          start0 + static_cast<int64_t>(s_flag[1]) + nch <= a.list_len;
+        if (!fits && t == 0) check_index(a, false, 8, s_flag[1]);
+        if (fits)
+            for (int32_t c = t; c < nch; c += kBlock)
+                store_item(next + start0 + s_flag[1] + c, beg + static_cast<int64_t>(c) * kSpecChunk,
+                           -(slot + 1), min(kSpecChunk, deg - c * kSpecChunk));
         __syncthreads();
     } else if (t == 0) {
         const int32_t c = static_cast<int32_t>(a.key[v] >> 32);
@@ -632,6 +675,9 @@ gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors
     a.hub_done = sh_done.as<int32_t>();
     a.hub_lose = sh_lose.as<int32_t>();
     a.hub_bm = sh_bm.as<uint32_t>();
+    a.n_hubs = hs.n_hubs;
+    a.hub_words_total = hub_words;
+    a.list_len = list_len;
     if (hs.n_hubs > 0) cudaMemsetAsync(a.hub_bm, 0, hub_words * 4, s);
     GC_LAUNCH(KID_SPEC_FILL, s, k_spec_fill<<<setup_grid, kBlock, 0, s>>>(a));
     gc_status st = GC_OK;
@@ -658,6 +704,11 @@ gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess && st == GC_OK) st = cuda_status(ce);
     if (st == GC_OK) st = status_from_err_bits(h.err);
+    if (h.err & kErrInternal) {
+        std::fprintf(stderr, "libgc: internal check %d failed at index %lld (access skipped)\n",
+                     h.bad_where, h.bad_index);
+        if (st == GC_OK) st = GC_ERR_CUDA;
+    }
     if (a.tune.spec_graph) note_launches(2 * static_cast<int64_t>(h.round));
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
