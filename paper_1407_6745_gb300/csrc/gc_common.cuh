@@ -35,7 +35,6 @@ constexpr uint32_t kErrBadGraph = 1u;
 constexpr uint32_t kErrTimeout = 2u;
 constexpr uint32_t kErrImproper = 4u;
 constexpr uint32_t kErrRoundLimit = 8u;
-constexpr uint32_t kErrInternal = 16u;  // an internal index check failed (access skipped)
 
 // Scheduling thresholds (runtime; tuned per workload).
 struct Tuning {
