@@ -289,6 +289,45 @@ def hubs(degrees, base_n: int, seed: int, device="cpu") -> CSRGraph:
 
 
 # ---------------------------------------------------------------------------
+# Batches of graphs
+# ---------------------------------------------------------------------------
+
+def batch_union(graphs, device=None) -> CSRGraph:
+    """Disjoint union of graphs as one CSR: graph i's vertices follow graph
+    i-1's, ids shifted accordingly."""
+    device = device if device is not None else graphs[0].offsets.device
+    offs, idxs = [torch.zeros(1, dtype=torch.int64, device=device)], []
+    vbase, ebase = 0, 0
+    for g in graphs:
+        offs.append(g.offsets[1:].to(device) + ebase)
+        idxs.append((g.idx.to(device).to(torch.int64) + vbase).to(torch.int32))
+        vbase += g.n
+        ebase += g.nnz
+    return CSRGraph(torch.cat(offs), torch.cat(idxs) if idxs else torch.zeros(0, dtype=torch.int32),
+                    f"batch{len(graphs)}")
+
+
+def batch_mix(count: int, seed: int, n_lo: float, n_hi: float, device="cpu"):
+    """The batch workload: `count` graphs, half G(n, p) with mean degree drawn
+    from U[8, 32], half 2D 5-point or 3D 7-point grids; n log-uniform in
+    [n_lo, n_hi].  Returns the graphs (each with its own ids)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        if i % 2 == 0:
+            out.append(erdos_renyi(max(n, 2), float(rng.uniform(8.0, 32.0)), seed=seed * 100003 + i,
+                                   device=device))
+        elif rng.random() < 0.5:
+            side = max(2, int(round(math.sqrt(n))))
+            out.append(grid_2d(side, side, device=device))
+        else:
+            side = max(2, int(round(n ** (1.0 / 3.0))))
+            out.append(stencil_3d(side, side, side, points=7, device=device))
+    return out
+
+
+# ---------------------------------------------------------------------------
 # The benchmark workloads
 # ---------------------------------------------------------------------------
 

@@ -157,6 +157,56 @@ gc_status gc_color_recolor(const gc_graph* g, gc_strategy strategy, int32_t X, u
  * (seed_lo, seed_hi), for v in [0, n).  out is device memory (uint32[n]). */
 gc_status gc_priorities(uint64_t seed, int64_t n, uint32_t* out, void* stream);
 
+/*
+ * Batches: many independent graphs colored and recolored together in the
+ * same launches.  The batch is one concatenated CSR (gc_graph) whose vertices
+ * are numbered globally; graph i owns the vertices [vertex_base, vertex_base +
+ * n) and every edge of a vertex stays inside its graph (caller's contract).
+ * The descriptors must tile [0, g->n) in order: vertex_base of the first is
+ * 0 and each next one starts where the previous one ends.  Priorities and
+ * Random-X draws use graph-local ids and the graph's own seed, so every
+ * graph's colors are exactly those gc_color / gc_recolor give it alone.
+ * (Not in the paper: a library extension for many-graph workloads.)
+ */
+typedef struct {
+    int64_t vertex_base;  /* first vertex of the graph in the batch            */
+    int64_t n;            /* vertices of the graph                             */
+    uint64_t seed;        /* keys priorities and Random-X draws                 */
+    int32_t X;            /* 1 = First Fit, > 1 = Random-X Fit                  */
+    int32_t perm;         /* gc_perm of its recoloring                          */
+    int32_t iterations;   /* recoloring iterations (>= 0)                       */
+    int32_t reserved;
+    uint64_t perm_seed;   /* keys GC_PERM_RANDOM                                */
+} gc_batch_graph;
+
+/*
+ * Speculative coloring of every graph of a batch (host descriptors).
+ * rounds_out / max_color_out (host, ngraphs entries each, may be NULL)
+ * receive each graph's round count and max color.
+ */
+gc_status gc_color_batch(const gc_graph* g, const gc_batch_graph* graphs, int32_t ngraphs,
+                         int32_t* colors_out, int32_t* rounds_out, int32_t* max_color_out,
+                         gc_stats* stats, void* stream);
+
+/*
+ * Recoloring of every graph of a batch, each with its own permutation,
+ * seed and iteration count; colors_in must be proper.  max_color_out (host,
+ * ngraphs entries, may be NULL) receives each graph's final max color.
+ * colors_out may alias colors_in.
+ */
+gc_status gc_recolor_batch(const gc_graph* g, const gc_batch_graph* graphs, int32_t ngraphs,
+                           const int32_t* colors_in, int32_t* colors_out, int32_t* max_color_out,
+                           gc_stats* stats, void* stream);
+
+/*
+ * Batch pipeline: gc_color_batch followed by gc_recolor_batch on its output
+ * (proper by construction: not re-validated), each graph with its own
+ * recoloring settings.  rounds_out / max_color_out as above (final colors).
+ */
+gc_status gc_color_recolor_batch(const gc_graph* g, const gc_batch_graph* graphs, int32_t ngraphs,
+                                 int32_t* colors_out, int32_t* rounds_out, int32_t* max_color_out,
+                                 gc_stats* stats, void* stream);
+
 /* Checks the coloring against the definition of Sec. 1 and the graph's
  * structure (GC_ERR_BAD_GRAPH if malformed). */
 gc_status gc_validate(const gc_graph* g, const int32_t* colors, gc_validation* out, void* stream);

@@ -20,7 +20,8 @@ import torch
 
 __all__ = [
     "GCError", "FIRST_FIT", "RANDOM_X_FIT", "PERM", "library_path", "load",
-    "gc_color", "gc_recolor", "gc_color_recolor", "gc_validate", "gc_validate_noalloc",
+    "gc_color", "gc_recolor", "gc_color_recolor", "gc_color_batch", "gc_recolor_batch",
+    "gc_color_recolor_batch", "gc_validate", "gc_validate_noalloc",
     "gc_check_graph",
     "gc_priorities", "gc_set_tuning", "gc_get_tuning", "gc_profile_enable", "gc_profile_read",
     "gc_kernel_launches", "gc_status_string", "gc_version",
@@ -63,6 +64,12 @@ class _Validation(ctypes.Structure):
                 ("first_bad_vertex", ctypes.c_int64)]
 
 
+class _BatchGraph(ctypes.Structure):
+    _fields_ = [("vertex_base", ctypes.c_int64), ("n", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("X", ctypes.c_int32), ("perm", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("perm_seed", ctypes.c_uint64)]
+
+
 class _KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
 
@@ -100,6 +107,12 @@ def load():
         lib.gc_validate_noalloc.argtypes = [G, P, ctypes.POINTER(_Validation), P]
         lib.gc_validate_noalloc.restype = ctypes.c_int
         lib.gc_check_graph.argtypes = [G, ctypes.POINTER(ctypes.c_int64), P]
+        B = ctypes.POINTER(_BatchGraph)
+        lib.gc_color_batch.argtypes = [G, B, ctypes.c_int32, P, P, P, S, P]
+        lib.gc_recolor_batch.argtypes = [G, B, ctypes.c_int32, P, P, P, S, P]
+        lib.gc_color_recolor_batch.argtypes = [G, B, ctypes.c_int32, P, P, P, S, P]
+        for f in ("gc_color_batch", "gc_recolor_batch", "gc_color_recolor_batch"):
+            getattr(lib, f).restype = ctypes.c_int
         lib.gc_priorities.argtypes = [ctypes.c_uint64, ctypes.c_int64, P, P]
         lib.gc_priorities.restype = ctypes.c_int
         lib.gc_set_tuning.argtypes = [ctypes.POINTER(_Tuning)]
@@ -226,6 +239,69 @@ def gc_color_recolor(offsets, idx, strategy="FF", X: int = 1, seed: int = 0, per
            "gc_color_recolor")
     vd = {k: getattr(val, k) for k, _ in _Validation._fields_} if validate else None
     return out, list(nc), _stats_dict(st), vd
+
+
+def _batch(graphs):
+    """graphs: list of dicts with n, seed, X (default 1), perm ('RV'...),
+    iterations (default 0), perm_seed (default 0); bases are laid out in order."""
+    arr = (_BatchGraph * len(graphs))()
+    base = 0
+    for i, d in enumerate(graphs):
+        arr[i].vertex_base = base
+        arr[i].n = int(d["n"])
+        arr[i].seed = int(d.get("seed", 0)) & (2**64 - 1)
+        arr[i].X = int(d.get("X", 1))
+        arr[i].perm = _perm(d.get("perm", "RV"))
+        arr[i].iterations = int(d.get("iterations", 0))
+        arr[i].perm_seed = int(d.get("perm_seed", 0)) & (2**64 - 1)
+        base += int(d["n"])
+    return arr, base
+
+
+def _batch_call(fn, where, offsets, idx, graphs, colors_in=None, out=None, stream=None):
+    lib = load()
+    g, keep = _graph(offsets, idx)
+    dev = keep[0].device
+    arr, total = _batch(graphs)
+    if total != g.n:
+        raise ValueError(f"graphs cover {total} vertices, the batch CSR has {g.n}")
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.int32, device=dev)
+    _check_colors(out, g.n, dev, "out")
+    ng = len(graphs)
+    rounds = (ctypes.c_int32 * ng)()
+    maxc = (ctypes.c_int32 * ng)()
+    st = _Stats()
+    if colors_in is None:
+        rc = getattr(lib, fn)(ctypes.byref(g), arr, ng, _ptr(out), rounds, maxc, ctypes.byref(st),
+                              _stream(dev, stream))
+    else:
+        _check_colors(colors_in, g.n, dev, "colors_in")
+        rc = getattr(lib, fn)(ctypes.byref(g), arr, ng, _ptr(colors_in), _ptr(out), maxc,
+                              ctypes.byref(st), _stream(dev, stream))
+    _check(rc, where)
+    return out, list(rounds), list(maxc), _stats_dict(st)
+
+
+def gc_color_batch(offsets, idx, graphs, out=None, stream=None):
+    """Speculative coloring of a batch of graphs laid out in one CSR.
+    Returns (colors, rounds per graph, max color per graph, stats)."""
+    return _batch_call("gc_color_batch", "gc_color_batch", offsets, idx, graphs, out=out, stream=stream)
+
+
+def gc_recolor_batch(offsets, idx, graphs, colors_in, out=None, stream=None):
+    """Recoloring of a batch (each graph's perm, perm_seed, iterations).
+    Returns (colors, max color per graph, stats)."""
+    out, _, maxc, st = _batch_call("gc_recolor_batch", "gc_recolor_batch", offsets, idx, graphs,
+                                   colors_in=colors_in, out=out, stream=stream)
+    return out, maxc, st
+
+
+def gc_color_recolor_batch(offsets, idx, graphs, out=None, stream=None):
+    """Coloring then recoloring of a batch, in one call.
+    Returns (colors, rounds per graph, final max color per graph, stats)."""
+    return _batch_call("gc_color_recolor_batch", "gc_color_recolor_batch", offsets, idx, graphs,
+                       out=out, stream=stream)
 
 
 def gc_validate(offsets, idx, colors, stream=None):

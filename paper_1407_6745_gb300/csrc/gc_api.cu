@@ -114,7 +114,8 @@ const char* const kKernelNames[] = {
     "k_spec_setup", "k_spec_fill", "k_tentative", "k_conflict", "k_priorities",
     "k_rc_bucket", "k_rc_validate", "k_rc_hist", "k_rc_order", "k_rc_scatter",
     "k_rc_recolor_coop", "k_rc_recolor_step", "k_validate", "k_validate_heavy",
-    "k_mark_present", "k_count_bits", "k_check_graph", "spec_rounds_graph"};
+    "k_mark_present", "k_count_bits", "k_check_graph", "spec_rounds_graph", "k_batch", "k_brc_hist",
+    "k_brc_order", "k_brc_segments"};
 static_assert(sizeof(kKernelNames) / sizeof(kKernelNames[0]) == KID_COUNT_,
               "one name per KernelId");
 std::atomic<bool> g_prof_on{false};
@@ -423,6 +424,82 @@ int32_t gc_profile_read(gc_kernel_time* out, int32_t max) {
         ++cnt;
     }
     return cnt;
+}
+
+static gc_status gc_color_batch_impl(const gc_graph* g, const gc_batch_graph* graphs, int32_t ngraphs,
+                                     int32_t* colors_out, int32_t* rounds_out, int32_t* max_color_out,
+                                     gc_stats* stats, void* stream) {
+    gc_status st = check_graph_args(g);
+    if (st != GC_OK) return st;
+    if (!graphs || ngraphs < 1 || (g->n > 0 && !colors_out)) return GC_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceGraph dg;
+    DeviceColors dc;
+    if ((st = dg.stage(g, s)) != GC_OK) return st;
+    if ((st = dc.stage(colors_out, g->n, g->mem, false, s)) != GC_OK) return st;
+    st = color_batch_device(dg.g, graphs, ngraphs, dc.d, rounds_out, max_color_out, stats, s);
+    if (st != GC_OK) return st;
+    return dc.unstage(colors_out, g->n, g->mem, s);
+}
+
+static gc_status gc_recolor_batch_impl(const gc_graph* g, const gc_batch_graph* graphs, int32_t ngraphs,
+                                       const int32_t* colors_in, int32_t* colors_out,
+                                       int32_t* max_color_out, gc_stats* stats, void* stream) {
+    gc_status st = check_graph_args(g);
+    if (st != GC_OK) return st;
+    if (!graphs || ngraphs < 1 || (g->n > 0 && (!colors_in || !colors_out))) return GC_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceGraph dg;
+    DeviceColors din;
+    if ((st = dg.stage(g, s)) != GC_OK) return st;
+    if ((st = din.stage(const_cast<int32_t*>(colors_in), g->n, g->mem, true, s)) != GC_OK) return st;
+    int32_t* dout = g->mem == GC_MEM_HOST ? din.d : colors_out;
+    st = recolor_batch_device(dg.g, graphs, ngraphs, din.d, dout, max_color_out, stats, s);
+    if (st != GC_OK) return st;
+    return din.unstage(colors_out, g->n, g->mem, s);
+}
+
+static gc_status gc_color_recolor_batch_impl(const gc_graph* g, const gc_batch_graph* graphs,
+                                             int32_t ngraphs, int32_t* colors_out, int32_t* rounds_out,
+                                             int32_t* max_color_out, gc_stats* stats, void* stream) {
+    gc_status st = check_graph_args(g);
+    if (st != GC_OK) return st;
+    if (!graphs || ngraphs < 1 || (g->n > 0 && !colors_out)) return GC_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceGraph dg;
+    DeviceColors dc;
+    if ((st = dg.stage(g, s)) != GC_OK) return st;
+    if ((st = dc.stage(colors_out, g->n, g->mem, false, s)) != GC_OK) return st;
+    st = color_recolor_batch_device(dg.g, graphs, ngraphs, dc.d, rounds_out, max_color_out, stats, s);
+    if (st != GC_OK) return st;
+    return dc.unstage(colors_out, g->n, g->mem, s);
+}
+
+gc_status gc_color_batch(const gc_graph* g, const gc_batch_graph* graphs, int32_t ngraphs,
+                         int32_t* colors_out, int32_t* rounds_out, int32_t* max_color_out,
+                         gc_stats* stats, void* stream) {
+    const gc_status st = gc_color_batch_impl(g, graphs, ngraphs, colors_out, rounds_out, max_color_out,
+                                             stats, stream);
+    prof_collect();
+    return st;
+}
+
+gc_status gc_recolor_batch(const gc_graph* g, const gc_batch_graph* graphs, int32_t ngraphs,
+                           const int32_t* colors_in, int32_t* colors_out, int32_t* max_color_out,
+                           gc_stats* stats, void* stream) {
+    const gc_status st = gc_recolor_batch_impl(g, graphs, ngraphs, colors_in, colors_out, max_color_out,
+                                               stats, stream);
+    prof_collect();
+    return st;
+}
+
+gc_status gc_color_recolor_batch(const gc_graph* g, const gc_batch_graph* graphs, int32_t ngraphs,
+                                 int32_t* colors_out, int32_t* rounds_out, int32_t* max_color_out,
+                                 gc_stats* stats, void* stream) {
+    const gc_status st = gc_color_recolor_batch_impl(g, graphs, ngraphs, colors_out, rounds_out,
+                                                     max_color_out, stats, stream);
+    prof_collect();
+    return st;
 }
 
 gc_status gc_validate_noalloc(const gc_graph* g, const int32_t* colors, gc_validation* out,

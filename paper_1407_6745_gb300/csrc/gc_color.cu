@@ -54,7 +54,23 @@ struct SpecArgs {
     unsigned long long cond;  // WHILE-node handle (graph mode)
     int32_t use_cond;
     int32_t round_limit;
+    // batches: graph of every vertex and the graphs' descriptors (nullptr for
+    // one graph), and the round in which every vertex kept its color
+    const int32_t* graph_of;
+    const BatchDesc* desc;
+    int32_t* win_round;
 };
+
+// Random-X index of v in `round`: the graph's own seed, X and local id.
+__device__ __forceinline__ uint32_t draw_index(const SpecArgs& a, int32_t v, int32_t round) {
+    if (a.graph_of) {
+        const BatchDesc& d = a.desc[a.graph_of[v]];
+        if (d.X <= 1) return 0u;
+        return scale_index(rxf_word(d.seed, static_cast<int32_t>(v - d.base), round),
+                           static_cast<uint32_t>(d.X));
+    }
+    return scale_index(rxf_word(a.seed, v, round), static_cast<uint32_t>(a.X));
+}
 
 // ---------------------------------------------------------------------------
 // Set-up: priorities, bucket sizes, then the round-0 work list (all vertices)
@@ -68,9 +84,17 @@ __global__ void __launch_bounds__(kBlock) k_spec_setup(SpecArgs a) {
         int32_t deg;
         row_of(a.g, v, beg, deg, &a.ctrl->err);
         my_max_deg = max(my_max_deg, deg);
-        const int b = bucket_of(deg, a.X, a.tune);
+        int32_t X = a.X, vl = v;
+        uint64_t seed = a.seed;
+        if (a.graph_of) {
+            const BatchDesc& d = a.desc[a.graph_of[v]];
+            X = d.X;
+            seed = d.seed;
+            vl = static_cast<int32_t>(v - d.base);
+        }
+        const int b = bucket_of(deg, X, a.tune);
         a.bucket[v] = static_cast<uint8_t>(b);
-        a.key[v] = prio_of(a.seed, v);  // tentative color 0
+        a.key[v] = prio_of(seed, vl);  // tentative color 0
         a.color[v] = 0;
         const unsigned act = __activemask();
         const unsigned peers = __match_any_sync(act, b);
@@ -168,7 +192,7 @@ __device__ __forceinline__ void tentative_group_tile(const SpecArgs& a, const Ro
     uint32_t j = 0;
     if (valid) {
         it = load_item(list + rt.start[b] + k);
-        if (kRXF) j = scale_index(rxf_word(a.seed, it.v, round), static_cast<uint32_t>(a.X));
+        if (kRXF) j = draw_index(a, it.v, round);
     }
     const SnapshotFetch fetch{a.color};
     const int32_t c = choose_reg<G, LanesUnroll<G>::U>(a.g, it.beg, it.deg, gl, j, fetch, &a.ctrl->err);
@@ -195,7 +219,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
         switch (b) {
         case 0: {
             const WorkItem it = load_item(list + rt.start[0] + first);
-            const uint32_t j = kRXF ? scale_index(rxf_word(a.seed, it.v, round), a.X) : 0u;
+            const uint32_t j = kRXF ? draw_index(a, it.v, round) : 0u;
             const int32_t c = choose_block<4>(a.g, it.beg, it.deg, j, fetch, sm.blk, &a.ctrl->err);
             if (threadIdx.x == 0) {
                 set_tent(a, it.v, c);
@@ -208,7 +232,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
             const int32_t k = first + w;
             if (k < rt.cnt[1]) {
                 const WorkItem it = load_item(list + rt.start[1] + k);
-                const uint32_t j = kRXF ? scale_index(rxf_word(a.seed, it.v, round), a.X) : 0u;
+                const uint32_t j = kRXF ? draw_index(a, it.v, round) : 0u;
                 const int32_t c = choose_warp<4>(a.g, it.beg, it.deg, j, fetch, sm.warp_bm[w], &a.ctrl->err);
                 if (lane_id() == 0) {
                     set_tent(a, it.v, c);
@@ -269,6 +293,7 @@ __device__ __forceinline__ void conflict_group_tile(const SpecArgs& a, const Rou
             const int32_t c = static_cast<int32_t>(a.key[it.v] >> 32);
             a.color[it.v] = c;
             my_max = max(my_max, c);
+            if (a.win_round) a.win_round[it.v] = a.ctrl->round;
         }
     }
     warp_append(leader && lose, it.beg, it.v, it.deg, &a.ctrl->cnt[par ^ 1][b], next, rt.start[b]);
@@ -300,6 +325,7 @@ __global__ void __launch_bounds__(kBlock) k_conflict(SpecArgs a) {
                     const int32_t c = static_cast<int32_t>(a.key[it.v] >> 32);
                     a.color[it.v] = c;
                     my_max = max(my_max, c);
+                    if (a.win_round) a.win_round[it.v] = round;
                 }
             }
             break;
@@ -408,8 +434,10 @@ gc_status rounds_in_graph(SpecArgs& a, int32_t X, int grid_t, int grid_c, cudaSt
     return cuda_status(e);
 }
 
-gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors_out,
-                       gc_stats* stats, cudaStream_t s) {
+// The speculative coloring; with graph_of / desc / win_round set, a batch.
+static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int32_t* graph_of,
+                            const BatchDesc* desc, int32_t* win_round, int32_t* colors_out,
+                            gc_stats* stats, cudaStream_t s) {
     if (g.n == 0) {
         if (stats) { std::memset(stats, 0, sizeof(*stats)); }
         return GC_OK;
@@ -433,6 +461,9 @@ gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors
     a.list0 = sc_l0.as<WorkItem>();
     a.list1 = sc_l1.as<WorkItem>();
     a.ctrl = sc_ctrl.as<SpecCtrl>();
+    a.graph_of = graph_of;
+    a.desc = desc;
+    a.win_round = win_round;
 
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -482,6 +513,120 @@ gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    return st;
+}
+
+gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors_out,
+                       gc_stats* stats, cudaStream_t s) {
+    return color_impl(g, X, seed, nullptr, nullptr, nullptr, colors_out, stats, s);
+}
+
+// ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+// Graph of every vertex, by binary search over the graphs' first vertices.
+__global__ void __launch_bounds__(kBlock) k_graph_of(int64_t n, const BatchDesc* desc, int32_t ng,
+                                                     int32_t* graph_of) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kBlock;
+    for (int64_t v = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; v < n; v += stride) {
+        int lo = 0, hi = ng - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (desc[mid].base <= v) lo = mid; else hi = mid - 1;
+        }
+        graph_of[v] = lo;
+    }
+}
+
+// Per-graph max of a color array and of the winning rounds (+1); graphs are
+// contiguous, so a warp mostly covers one or two of them.
+__global__ void __launch_bounds__(kBlock) k_batch_stats(int64_t n, const int32_t* graph_of,
+                                                        const int32_t* colors, const int32_t* win_round,
+                                                        int32_t* g_maxc, int32_t* g_rounds) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kBlock;
+    for (int64_t v = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; v < n; v += stride) {
+        const int32_t gi = graph_of[v];
+        int32_t c = colors[v];
+        int32_t r = win_round ? win_round[v] + 1 : 0;
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, gi);
+        c = __reduce_max_sync(peers, c);
+        r = __reduce_max_sync(peers, r);
+        if (lane_id() == __ffs(peers) - 1) {
+            atomicMax(&g_maxc[gi], c);
+            if (g_rounds) atomicMax(&g_rounds[gi], r);
+        }
+    }
+}
+
+gc_status batch_layout(const Graph& g, const gc_batch_graph* graphs, int32_t ng, int32_t* max_x) {
+    if (ng < 1 || !graphs) return GC_ERR_INVALID_ARG;
+    int64_t next = 0;
+    int32_t mx = 1;
+    for (int32_t i = 0; i < ng; ++i) {
+        const gc_batch_graph& d = graphs[i];
+        if (d.vertex_base != next || d.n < 0 || d.X < 1 || d.iterations < 0 || d.perm < 0 || d.perm > 3)
+            return GC_ERR_INVALID_ARG;
+        next += d.n;
+        mx = std::max(mx, d.X);
+    }
+    if (next != g.n) return GC_ERR_INVALID_ARG;
+    *max_x = mx;
+    return GC_OK;
+}
+
+gc_status batch_graph_of(const Graph& g, const BatchDesc* d_desc, int32_t ng, int32_t* graph_of,
+                         cudaStream_t s) {
+    if (g.n == 0) return GC_OK;
+    const int grid = static_cast<int>(std::min<int64_t>((g.n + kBlock - 1) / kBlock,
+                                                        persistent_grid(current_tuning())));
+    GC_LAUNCH(KID_BATCH, s, k_graph_of<<<grid, kBlock, 0, s>>>(g.n, d_desc, ng, graph_of));
+    return GC_OK;
+}
+
+gc_status batch_max_colors(const Graph& g, const int32_t* graph_of, const int32_t* colors,
+                           const int32_t* win_round, int32_t ng, int32_t* max_color_out,
+                           int32_t* rounds_out, cudaStream_t s) {
+    Scratch sm, sr;
+    if (!sm.alloc(ng * 4, s) || !sr.alloc(ng * 4, s)) return GC_ERR_OOM;
+    cudaMemsetAsync(sm.p, 0, ng * 4, s);
+    cudaMemsetAsync(sr.p, 0, ng * 4, s);
+    if (g.n > 0) {
+        const int grid = static_cast<int>(std::min<int64_t>((g.n + kBlock - 1) / kBlock,
+                                                            persistent_grid(current_tuning())));
+        GC_LAUNCH(KID_BATCH, s,
+                  k_batch_stats<<<grid, kBlock, 0, s>>>(g.n, graph_of, colors, win_round,
+                                                         sm.as<int32_t>(), win_round ? sr.as<int32_t>() : nullptr));
+    }
+    cudaError_t e = cudaSuccess;
+    if (max_color_out) e = cudaMemcpyAsync(max_color_out, sm.p, ng * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && rounds_out)
+        e = cudaMemcpyAsync(rounds_out, sr.p, ng * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_status(e);
+}
+
+gc_status color_batch_device(const Graph& g, const gc_batch_graph* graphs, int32_t ng,
+                             int32_t* colors_out, int32_t* rounds_out, int32_t* max_color_out,
+                             gc_stats* stats, cudaStream_t s) {
+    int32_t max_x = 1;
+    gc_status st = batch_layout(g, graphs, ng, &max_x);
+    if (st != GC_OK) return st;
+    static_assert(sizeof(BatchDesc) == sizeof(gc_batch_graph), "descriptor layout");
+    Scratch sd, sgo, swr;
+    if (!sd.alloc(static_cast<size_t>(ng) * sizeof(BatchDesc), s) || !sgo.alloc(g.n * 4 + 4, s) ||
+        !swr.alloc(g.n * 4 + 4, s))
+        return GC_ERR_OOM;
+    cudaError_t e = cudaMemcpyAsync(sd.p, graphs, static_cast<size_t>(ng) * sizeof(BatchDesc),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    const BatchDesc* d_desc = sd.as<BatchDesc>();
+    int32_t* graph_of = sgo.as<int32_t>();
+    batch_graph_of(g, d_desc, ng, graph_of, s);
+    st = color_impl(g, max_x, 0, graph_of, d_desc, swr.as<int32_t>(), colors_out, stats, s);
+    if (st != GC_OK) return st;
+    if (rounds_out || max_color_out)
+        st = batch_max_colors(g, graph_of, colors_out, swr.as<int32_t>(), ng, max_color_out, rounds_out, s);
     return st;
 }
 

@@ -58,6 +58,18 @@ __host__ __device__ inline int bucket_of(int64_t deg, int32_t X, const Tuning& t
     return deg <= t.warp_max_deg ? 1 : 0;
 }
 
+// One graph of a batch (same layout as gc_batch_graph).
+struct BatchDesc {
+    int64_t base;
+    int64_t n;
+    uint64_t seed;
+    int32_t X;
+    int32_t perm;
+    int32_t iterations;
+    int32_t reserved;
+    uint64_t perm_seed;
+};
+
 struct Graph {
     const int64_t* off;
     const int32_t* idx;

@@ -40,7 +40,8 @@ enum KernelId {
     KID_SPEC_SETUP, KID_SPEC_FILL, KID_TENTATIVE, KID_CONFLICT, KID_PRIORITIES,
     KID_RC_BUCKET, KID_RC_VALIDATE, KID_RC_HIST, KID_RC_ORDER, KID_RC_SCATTER,
     KID_RC_RECOLOR, KID_RC_STEP, KID_VALIDATE, KID_VALIDATE_HEAVY, KID_MARK_PRESENT,
-    KID_COUNT_BITS, KID_CHECK_GRAPH, KID_SPEC_GRAPH, KID_COUNT_
+    KID_COUNT_BITS, KID_CHECK_GRAPH, KID_SPEC_GRAPH, KID_BATCH, KID_BRC_HIST, KID_BRC_ORDER,
+    KID_BRC_SEGMENTS, KID_COUNT_
 };
 void prof_begin(KernelId k, cudaStream_t s);
 void prof_end(KernelId k, cudaStream_t s);
@@ -88,6 +89,24 @@ gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors
 gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_in, bool trusted,
                          int32_t perm, int32_t iterations, uint64_t seed, int32_t* colors_out,
                          int32_t* ncolors_per_iter, gc_stats* stats, cudaStream_t s);
+
+// Batches (see gc_batch_graph): descriptor checks, graph of each vertex,
+// per-graph statistics.
+gc_status batch_layout(const Graph& g, const gc_batch_graph* graphs, int32_t ng, int32_t* max_x);
+gc_status batch_graph_of(const Graph& g, const BatchDesc* d_desc, int32_t ng, int32_t* graph_of,
+                         cudaStream_t s);
+gc_status batch_max_colors(const Graph& g, const int32_t* graph_of, const int32_t* colors,
+                           const int32_t* win_round, int32_t ng, int32_t* max_color_out,
+                           int32_t* rounds_out, cudaStream_t s);
+gc_status color_batch_device(const Graph& g, const gc_batch_graph* graphs, int32_t ng,
+                             int32_t* colors_out, int32_t* rounds_out, int32_t* max_color_out,
+                             gc_stats* stats, cudaStream_t s);
+gc_status recolor_batch_device(const Graph& g, const gc_batch_graph* graphs, int32_t ng,
+                               const int32_t* colors_in, int32_t* colors_out, int32_t* max_color_out,
+                               gc_stats* stats, cudaStream_t s);
+gc_status color_recolor_batch_device(const Graph& g, const gc_batch_graph* graphs, int32_t ng,
+                                     int32_t* colors_out, int32_t* rounds_out, int32_t* max_color_out,
+                                     gc_stats* stats, cudaStream_t s);
 
 gc_status priorities_device(uint64_t seed, int64_t n, uint32_t* out, cudaStream_t s);
 

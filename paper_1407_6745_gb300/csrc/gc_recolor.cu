@@ -87,6 +87,19 @@ struct RcArgs {
     uint32_t* hub_bm;
     int32_t hub_words;
     RcCtrl* ctrl;
+    // batches (nullptr for one graph): graph of every vertex, descriptors,
+    // and the start of each graph's colors in the (graph, color) tables
+    // cls_cnt / cls_units / rank_of / g*
+    const int32_t* graph_of;
+    const BatchDesc* desc;
+    const int64_t* cls_base;
+    int32_t ngraphs;
+    int32_t fuse_hist;    // 1: the recoloring kernel fills nxt_cnt (one graph only)
+    int32_t* gpresent;    // per (graph, color): present colors, sizes, order, shuffle
+    int32_t* gpsize;
+    int32_t* gorder;
+    int32_t* gjtab;
+    int32_t* seg_cnt;     // list entries per global segment (rank, bucket)
 };
 
 __device__ __forceinline__ int32_t ld_relaxed(const int32_t* p) {
@@ -217,6 +230,41 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t x, OrderShared& 
     return r;
 }
 
+// Segment starts (list entries) and tile prefix (warp tiles) of the k
+// ranks x kNB buckets, class-major; units(sg) gives a segment's entries.
+template <class Units>
+__device__ __forceinline__ void build_segments(const RcArgs& a, int32_t k, OrderShared& s, Units&& units) {
+    const int t = threadIdx.x;
+    const int32_t nseg = k * kNB;
+    int32_t vbase = 0, tbase = 0;
+    for (int32_t s0 = 0; s0 < nseg; s0 += kOrderThreads) {
+        const int32_t sg = s0 + t;
+        int32_t cnt = 0, tiles = 0;
+        if (sg < nseg) {
+            const int b = sg % kNB;
+            cnt = units(sg);
+            tiles = (cnt + warp_tile(b) - 1) / warp_tile(b);
+            a.fill[sg] = 0;
+        }
+        int32_t vt, tt;
+        const int32_t vp = block_exclusive_scan(cnt, s, vt);
+        const int32_t tp = block_exclusive_scan(tiles, s, tt);
+        if (sg < nseg) {
+            a.seg_start[sg] = vbase + vp;
+            a.tile_prefix[sg] = tbase + tp;
+        }
+        vbase += vt;
+        tbase += tt;
+    }
+    if (t == 0) {
+        a.seg_start[nseg] = vbase;
+        a.tile_prefix[nseg] = tbase;
+        a.ctrl->k = k;
+        a.ctrl->total_tiles = tbase;
+        a.ctrl->hub_next = 0;
+    }
+}
+
 __global__ void __launch_bounds__(kOrderThreads) k_rc_order(RcArgs a) {
     __shared__ OrderShared s;
     const int t = threadIdx.x;
@@ -281,35 +329,11 @@ __global__ void __launch_bounds__(kOrderThreads) k_rc_order(RcArgs a) {
     // rank of every present color; segments (class-major, bucket-minor) in
     // list entries and in warp tiles
     for (int32_t p = t; p < k; p += kOrderThreads) a.rank_of[a.order[p]] = p;
-    const int32_t nseg = k * kNB;
-    int32_t vbase = 0, tbase = 0;
-    for (int32_t s0 = 0; s0 < nseg; s0 += kOrderThreads) {
-        const int32_t sg = s0 + t;
-        int32_t cnt = 0, tiles = 0;
-        if (sg < nseg) {
-            const int b = sg % kNB;
-            const int32_t c = a.order[sg / kNB];
-            cnt = b == 0 ? a.cls_units[c] : a.cls_cnt[c * kNB + b];
-            tiles = (cnt + warp_tile(b) - 1) / warp_tile(b);
-            a.fill[sg] = 0;
-        }
-        int32_t vt, tt;
-        const int32_t vp = block_exclusive_scan(cnt, s, vt);
-        const int32_t tp = block_exclusive_scan(tiles, s, tt);
-        if (sg < nseg) {
-            a.seg_start[sg] = vbase + vp;
-            a.tile_prefix[sg] = tbase + tp;
-        }
-        vbase += vt;
-        tbase += tt;
-    }
-    if (t == 0) {
-        a.seg_start[nseg] = vbase;
-        a.tile_prefix[nseg] = tbase;
-        a.ctrl->k = k;
-        a.ctrl->total_tiles = tbase;
-        a.ctrl->hub_next = 0;
-    }
+    build_segments(a, k, s, [&](int32_t sg) {
+        const int b = sg % kNB;
+        const int32_t c = a.order[sg / kNB];
+        return b == 0 ? a.cls_units[c] : a.cls_cnt[c * kNB + b];
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -332,7 +356,19 @@ struct ScatterInfo {
 __device__ __forceinline__ ScatterInfo scatter_info(const RcArgs& a, int32_t v) {
     ScatterInfo si;
     const int b = a.bucket[v];
-    si.sg = a.rank_of[a.old_c[v]] * kNB + b;
+    int64_t key = a.old_c[v];
+    if (a.graph_of) {  // batch: the graph's own class ranks; a finished graph keeps its colors
+        const int32_t gi = a.graph_of[v];
+        if (a.iteration >= a.desc[gi].iterations) {
+            si.sg = -1;
+            si.units = 0;
+            si.beg = 0;
+            si.deg = 0;
+            return si;
+        }
+        key += a.cls_base[gi];
+    }
+    si.sg = a.rank_of[key] * kNB + b;
     row_of(a.g, v, si.beg, si.deg, &a.ctrl->err);
     si.units = b == 0 ? chunks_of(si.deg) : 1;
     return si;
@@ -381,6 +417,10 @@ __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
         for (int64_t i = lo + threadIdx.x; i < hi; i += kBlock) {
             const int32_t v = static_cast<int32_t>(i);
             const ScatterInfo si = scatter_info(a, v);
+            if (si.sg < 0) {
+                a.new_c[v] = a.old_c[v];
+                continue;
+            }
             const int32_t off = reserve(a.fill, si);
             place(a, v, si, a.seg_start[si.sg] + off);
         }
@@ -390,7 +430,7 @@ __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
     __syncthreads();
     for (int64_t i = lo + threadIdx.x; i < hi; i += kBlock) {
         const ScatterInfo si = scatter_info(a, static_cast<int32_t>(i));
-        reserve(s_cnt, si);
+        if (si.sg >= 0) reserve(s_cnt, si);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nseg; i += kBlock) {
@@ -402,6 +442,10 @@ __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
     for (int64_t i = lo + threadIdx.x; i < hi; i += kBlock) {
         const int32_t v = static_cast<int32_t>(i);
         const ScatterInfo si = scatter_info(a, v);
+        if (si.sg < 0) {
+            a.new_c[v] = a.old_c[v];
+            continue;
+        }
         const int32_t off = reserve(s_cnt, si);
         place(a, v, si, s_base[si.sg] + off);
     }
@@ -567,6 +611,7 @@ constexpr int kSegSmem = 1024;
 // unfinished tile has finished all its earlier tiles, so it is working on
 // that tile: the waits always end.
 __device__ __forceinline__ NextHist setup_next_hist(const RcArgs& a, int32_t* s_hist) {
+    if (!a.fuse_hist) return NextHist{nullptr, nullptr, nullptr, 0};  // cap 0: add() is a no-op
     const int32_t entries = (a.cap + 1) * kNB;
     const bool local = entries <= kRcHistSmem;
     if (local)
@@ -635,6 +680,115 @@ __global__ void __launch_bounds__(kBlock, 5) k_rc_recolor_step(RcArgs a, int32_t
     warp_add(&a.ctrl->edges, edges);
     warp_max(&a.ncolors[a.iteration + 1], my_max);
     flush_next_hist(a, nh);
+}
+
+// ---------------------------------------------------------------------------
+// Batches: per-graph class histograms and orders, global (rank, bucket)
+// segments.  A vertex waits only on neighbors of its own graph of a smaller
+// rank, and ranks are global segment keys, so the cooperative launch above
+// serves the whole batch unchanged.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_brc_hist(RcArgs a) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kBlock;
+    for (int64_t v = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; v < a.g.n; v += stride) {
+        const int32_t gi = a.graph_of[v];
+        if (a.iteration >= a.desc[gi].iterations) continue;
+        const int64_t base = a.cls_base[gi];
+        const int32_t maxc = static_cast<int32_t>(a.cls_base[gi + 1] - base - 1);
+        const int32_t c = a.old_c[v];
+        if (c < 1 || c > maxc) {
+            atomicOr(&a.ctrl->err, kErrImproper);
+            continue;
+        }
+        const int b = a.bucket[v];
+        const int64_t key = base + c;
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, static_cast<uint32_t>(key * kNB + b));
+        if (lane_id() == __ffs(peers) - 1) atomicAdd(&a.cls_cnt[key * kNB + b], __popc(peers));
+        if (b == 0) {
+            int64_t rb;
+            int32_t deg;
+            row_of(a.g, static_cast<int32_t>(v), rb, deg, &a.ctrl->err);
+            atomicAdd(&a.cls_units[key], chunks_of(deg));
+        }
+    }
+}
+
+// One warp per graph: present classes, the graph's permutation (the rules of
+// k_rc_order), the rank of each color, and the global segment counts.
+__global__ void __launch_bounds__(kBlock) k_brc_order(RcArgs a) {
+    const int l = lane_id();
+    const int32_t warps = gridDim.x * kWarps;
+    for (int32_t gi = blockIdx.x * kWarps + (threadIdx.x >> 5); gi < a.ngraphs; gi += warps) {
+        const BatchDesc d = a.desc[gi];
+        if (a.iteration >= d.iterations) continue;
+        const int64_t base = a.cls_base[gi];
+        const int32_t maxc = static_cast<int32_t>(a.cls_base[gi + 1] - base - 1);
+        int32_t* present = a.gpresent + base;
+        int32_t* psize = a.gpsize + base;
+        int32_t* order = a.gorder + base;
+        int32_t k = 0;
+        for (int32_t c0 = 1; c0 <= maxc; c0 += 32) {
+            const int32_t c = c0 + l;
+            int32_t size = 0;
+            if (c <= maxc)
+                for (int b = 0; b < kNB; ++b) size += a.cls_cnt[(base + c) * kNB + b];
+            const uint32_t bal = __ballot_sync(kFull, size > 0);
+            if (size > 0) {
+                const int32_t pos = k + __popc(bal & ((1u << l) - 1u));
+                present[pos] = c;
+                psize[pos] = size;
+            }
+            k += __popc(bal);
+        }
+        __syncwarp();
+        if (d.perm == 0) {
+            for (int32_t i = l; i < k; i += 32) order[i] = present[k - 1 - i];
+        } else if (d.perm == 1 || d.perm == 2) {
+            const bool noninc = d.perm == 1;
+            for (int32_t i = l; i < k; i += 32) {
+                const int32_t si = psize[i];
+                int32_t r = 0;
+                for (int32_t j = 0; j < k; ++j) {
+                    const int32_t sj = psize[j];
+                    r += noninc ? (sj > si || (sj == si && j < i)) : (sj < si || (sj == si && j < i));
+                }
+                order[r] = present[i];
+            }
+        } else {
+            int32_t* jtab = a.gjtab + base;
+            for (int32_t i = l; i < k; i += 32) {
+                jtab[i] = i == 0 ? 0
+                                 : static_cast<int32_t>(scale_index(perm_word(d.perm_seed, i, a.iteration),
+                                                                    static_cast<uint32_t>(i + 1)));
+                order[i] = present[i];
+            }
+            __syncwarp();
+            if (l == 0)
+                for (int32_t i = k - 1; i >= 1; --i) {
+                    const int32_t j = jtab[i];
+                    const int32_t x = order[i];
+                    order[i] = order[j];
+                    order[j] = x;
+                }
+        }
+        __syncwarp();
+        for (int32_t p = l; p < k; p += 32) {
+            const int32_t c = order[p];
+            a.rank_of[base + c] = p;
+            for (int b = 0; b < kNB; ++b) {
+                const int32_t u = b == 0 ? a.cls_units[base + c] : a.cls_cnt[(base + c) * kNB + b];
+                if (u) atomicAdd(&a.seg_cnt[p * kNB + b], u);
+            }
+        }
+        if (l == 0) atomicMax(&a.ctrl->k, k);
+    }
+}
+
+__global__ void __launch_bounds__(kOrderThreads) k_brc_segments(RcArgs a) {
+    __shared__ OrderShared s;
+    const int32_t k = a.ctrl->k;
+    build_segments(a, k, s, [&](int32_t sg) { return a.seg_cnt[sg]; });
 }
 
 // ---------------------------------------------------------------------------
@@ -729,6 +883,7 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
     a.hub_done = sc_hd.as<int32_t>();
     a.hub_bm = sc_hb.as<uint32_t>();
     a.hub_words = hub_words;
+    a.fuse_hist = 1;
     cudaMemsetAsync(a.ncolors, 0, (iterations + 1) * 4, s);
 
     cudaEvent_t e0, e1;
@@ -803,6 +958,209 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    return st;
+}
+
+// Batch recoloring: every graph recolored with its own permutation, seed and
+// iteration count; a graph past its count keeps its colors.
+static gc_status recolor_batch_impl(const Graph& g, const gc_batch_graph* graphs, int32_t ng,
+                                    const int32_t* colors_in, bool trusted, const int32_t* max_in,
+                                    int32_t* colors_out, int32_t* max_color_out, gc_stats* stats,
+                                    cudaStream_t s) {
+    int32_t max_x = 1;
+    gc_status st = batch_layout(g, graphs, ng, &max_x);
+    if (st != GC_OK) return st;
+    const int64_t n = g.n;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    int32_t iters = 0;
+    for (int32_t i = 0; i < ng; ++i) iters = std::max(iters, graphs[i].iterations);
+    const Tuning tune = current_tuning();
+    const int grid = persistent_grid(tune);
+    const int vgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, grid)));
+    const int coop_capacity = sm_count() * occupancy_of(reinterpret_cast<const void*>(k_rc_recolor_coop), kBlock);
+    const int grid_rc = std::min(resident_grid(k_rc_recolor_coop, tune), coop_capacity);
+    const int grid_step = resident_grid(k_rc_recolor_step, tune);
+    const int grid_sc = static_cast<int>(std::max<int64_t>(
+        1, std::min<int64_t>((n + kBlock - 1) / kBlock, resident_grid(k_rc_scatter, tune))));
+    const int grid_go = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((ng + kWarps - 1) / kWarps, grid)));
+    cudaError_t ce;
+
+    Scratch sc_ctrl, sc_bucket, sc_desc, sc_gof;
+    if (!sc_ctrl.alloc(sizeof(RcCtrl), s) || !sc_bucket.alloc(n + 1, s) ||
+        !sc_desc.alloc(static_cast<size_t>(ng) * sizeof(BatchDesc), s) || !sc_gof.alloc(n * 4 + 4, s))
+        return GC_ERR_OOM;
+    ce = cudaMemcpyAsync(sc_desc.p, graphs, static_cast<size_t>(ng) * sizeof(BatchDesc), cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    RcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.tune = tune;
+    a.old_c = colors_in;
+    a.bucket = sc_bucket.as<uint8_t>();
+    a.ctrl = sc_ctrl.as<RcCtrl>();
+    a.desc = sc_desc.as<BatchDesc>();
+    a.graph_of = sc_gof.as<int32_t>();
+    a.ngraphs = ng;
+    batch_graph_of(g, a.desc, ng, sc_gof.as<int32_t>(), s);
+    cudaMemsetAsync(a.ctrl, 0, sizeof(RcCtrl), s);
+    if (n > 0) {
+        GC_LAUNCH(KID_RC_BUCKET, s, k_rc_bucket<<<vgrid, kBlock, 0, s>>>(a));
+        if (!trusted) GC_LAUNCH(KID_RC_VALIDATE, s, k_rc_validate<<<grid, kBlock, 0, s>>>(a));
+    }
+    RcCtrl h;
+    ce = cudaMemcpyAsync(&h, a.ctrl, sizeof(RcCtrl), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    if (h.err & kErrBadGraph) return GC_ERR_BAD_GRAPH;
+    if (h.err & kErrImproper) return GC_ERR_IMPROPER_INPUT;
+    // each graph's max input color sizes its rows of the (graph, color) tables
+    std::vector<int32_t> gmax(ng, 0);
+    if (trusted && max_in) {
+        std::copy(max_in, max_in + ng, gmax.begin());
+    } else {
+        st = batch_max_colors(g, a.graph_of, colors_in, nullptr, ng, gmax.data(), nullptr, s);
+        if (st != GC_OK) return st;
+    }
+    std::vector<int64_t> base(static_cast<size_t>(ng) + 1, 0);
+    int32_t cap = 1;
+    for (int32_t i = 0; i < ng; ++i) {
+        base[i + 1] = base[i] + gmax[i] + 1;
+        cap = std::max(cap, gmax[i]);
+    }
+    const int64_t T = base[ng];
+    if (iters == 0 || n == 0) {
+        if (colors_out != colors_in && n > 0)
+            cudaMemcpyAsync(colors_out, colors_in, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
+        if (max_color_out) std::copy(gmax.begin(), gmax.end(), max_color_out);
+        return cuda_status(cudaStreamSynchronize(s));
+    }
+    const int64_t ent = static_cast<int64_t>(cap + 1) * kNB;
+    const int32_t hub_words = (cap + 1 + 31) / 32;
+    const int64_t hubs = std::max<int64_t>(1, h.n_heavy);
+    const int64_t list_len = n + (static_cast<int64_t>(g.nnz) / kChunk) + h.n_heavy;
+    Scratch sc_base, sc_cls, sc_units, sc_rank, sc_gp, sc_gs, sc_go, sc_gj, sc_segc, sc_seg, sc_tiles,
+        sc_fill, sc_list, sc_alt, sc_ncol, sc_hv, sc_hn, sc_hd, sc_hb;
+    if (!sc_base.alloc((ng + 1) * 8, s) || !sc_cls.alloc(T * kNB * 4, s) || !sc_units.alloc(T * 4, s) ||
+        !sc_rank.alloc(T * 4, s) || !sc_gp.alloc(T * 4, s) || !sc_gs.alloc(T * 4, s) ||
+        !sc_go.alloc(T * 4, s) || !sc_gj.alloc(T * 4, s) || !sc_segc.alloc(ent * 4, s) ||
+        !sc_seg.alloc((ent + 1) * 4, s) || !sc_tiles.alloc((ent + 1) * 4, s) || !sc_fill.alloc(ent * 4, s) ||
+        !sc_list.alloc(list_len * sizeof(WorkItem), s) || !sc_alt.alloc(n * 4, s) ||
+        !sc_ncol.alloc((iters + 1) * 4, s) || !sc_hv.alloc(hubs * 4, s) || !sc_hn.alloc(hubs * 4, s) ||
+        !sc_hd.alloc(hubs * 4, s) || !sc_hb.alloc(hubs * hub_words * 4, s))
+        return GC_ERR_OOM;
+    ce = cudaMemcpyAsync(sc_base.p, base.data(), (ng + 1) * 8, cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    a.cap = cap;
+    a.cls_base = sc_base.as<int64_t>();
+    a.cls_cnt = sc_cls.as<int32_t>();
+    a.cls_units = sc_units.as<int32_t>();
+    a.rank_of = sc_rank.as<int32_t>();
+    a.gpresent = sc_gp.as<int32_t>();
+    a.gpsize = sc_gs.as<int32_t>();
+    a.gorder = sc_go.as<int32_t>();
+    a.gjtab = sc_gj.as<int32_t>();
+    a.seg_cnt = sc_segc.as<int32_t>();
+    a.seg_start = sc_seg.as<int32_t>();
+    a.tile_prefix = sc_tiles.as<int32_t>();
+    a.fill = sc_fill.as<int32_t>();
+    a.list = sc_list.as<WorkItem>();
+    a.ncolors = sc_ncol.as<int32_t>();
+    a.hub_v = sc_hv.as<int32_t>();
+    a.hub_nch = sc_hn.as<int32_t>();
+    a.hub_done = sc_hd.as<int32_t>();
+    a.hub_bm = sc_hb.as<uint32_t>();
+    a.hub_words = hub_words;
+    a.fuse_hist = 0;
+    cudaMemsetAsync(a.ncolors, 0, (iters + 1) * 4, s);
+
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    int32_t* alt = sc_alt.as<int32_t>();
+    const int32_t* cur = colors_in;
+    std::vector<int32_t> tp;
+    for (int32_t it = 0; it < iters && st == GC_OK; ++it) {
+        int32_t* dst = (it % 2 == 0) ? alt : colors_out;
+        a.iteration = it;
+        a.old_c = cur;
+        a.new_c = dst;
+        cudaMemsetAsync(a.cls_cnt, 0, T * kNB * 4, s);
+        cudaMemsetAsync(a.cls_units, 0, T * 4, s);
+        cudaMemsetAsync(a.seg_cnt, 0, ent * 4, s);
+        cudaMemsetAsync(&a.ctrl->k, 0, sizeof(int32_t), s);
+        GC_LAUNCH(KID_BRC_HIST, s, k_brc_hist<<<vgrid, kBlock, 0, s>>>(a));
+        GC_LAUNCH(KID_BRC_ORDER, s, k_brc_order<<<grid_go, kBlock, 0, s>>>(a));
+        GC_LAUNCH(KID_BRC_SEGMENTS, s, k_brc_segments<<<1, kOrderThreads, 0, s>>>(a));
+        GC_LAUNCH(KID_RC_SCATTER, s, k_rc_scatter<<<grid_sc, kBlock, 0, s>>>(a));
+        if (tune.recolor_mode == 0) {
+            void* args[] = {&a};
+            cudaError_t le;
+            GC_LAUNCH(KID_RC_RECOLOR, s,
+                      le = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_rc_recolor_coop),
+                                                       dim3(grid_rc), dim3(kBlock), args, 0, s));
+            if (le != cudaSuccess) { st = cuda_status(le); break; }
+        } else {
+            RcCtrl hc;
+            ce = cudaMemcpyAsync(&hc, a.ctrl, sizeof(RcCtrl), cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+            if (ce != cudaSuccess) { st = cuda_status(ce); break; }
+            tp.resize(static_cast<size_t>(hc.k) * kNB + 1);
+            ce = cudaMemcpy(tp.data(), a.tile_prefix, tp.size() * 4, cudaMemcpyDeviceToHost);
+            if (ce != cudaSuccess) { st = cuda_status(ce); break; }
+            for (int32_t p = 0; p < hc.k; ++p) {
+                const int32_t t0 = tp[p * kNB], t1 = tp[(p + 1) * kNB];
+                if (t1 <= t0) continue;
+                const int g2 = std::min(grid_step, (t1 - t0 + kWarps - 1) / kWarps);
+                GC_LAUNCH(KID_RC_STEP, s, k_rc_recolor_step<<<g2, kBlock, 0, s>>>(a, p, t0, t1));
+            }
+        }
+        cur = dst;
+    }
+    if (st == GC_OK && cur != colors_out)
+        cudaMemcpyAsync(colors_out, cur, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
+    cudaEventRecord(e1, s);
+    ce = cudaMemcpyAsync(&h, a.ctrl, sizeof(RcCtrl), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess && st == GC_OK) st = cuda_status(ce);
+    if (st == GC_OK) st = status_from_err_bits(h.err);
+    if (st == GC_OK && max_color_out)
+        st = batch_max_colors(g, a.graph_of, colors_out, nullptr, ng, max_color_out, nullptr, s);
+    if (stats) {
+        stats->iterations = iters;
+        stats->edges_examined = static_cast<int64_t>(h.edges);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        stats->ms_recolor = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+gc_status recolor_batch_device(const Graph& g, const gc_batch_graph* graphs, int32_t ng,
+                               const int32_t* colors_in, int32_t* colors_out, int32_t* max_color_out,
+                               gc_stats* stats, cudaStream_t s) {
+    return recolor_batch_impl(g, graphs, ng, colors_in, false, nullptr, colors_out, max_color_out,
+                              stats, s);
+}
+
+gc_status color_recolor_batch_device(const Graph& g, const gc_batch_graph* graphs, int32_t ng,
+                                     int32_t* colors_out, int32_t* rounds_out, int32_t* max_color_out,
+                                     gc_stats* stats, cudaStream_t s) {
+    std::vector<int32_t> cmax(std::max(ng, 1));
+    gc_stats cs;
+    gc_status st = color_batch_device(g, graphs, ng, colors_out, rounds_out, cmax.data(), &cs, s);
+    if (st != GC_OK) return st;
+    gc_stats rs;
+    st = recolor_batch_impl(g, graphs, ng, colors_out, true, cmax.data(), colors_out, max_color_out,
+                            &rs, s);
+    if (stats) {
+        *stats = cs;
+        stats->iterations = rs.iterations;
+        stats->edges_examined = cs.edges_examined + rs.edges_examined;
+        stats->ms_recolor = rs.ms_recolor;
+    }
     return st;
 }
 
