@@ -270,6 +270,20 @@ gc_status gc_set_tuning(const gc_tuning* t);
 /* Reads the knobs in force. */
 gc_status gc_get_tuning(gc_tuning* out);
 
+/*
+ * Autotuner: times gc_color_recolor on the caller's graph (device memory) for
+ * candidate scheduling knobs, by coordinate descent from the knobs in force
+ * (lane-group thresholds, warp_max_deg, recolor_mode, spec_graph, grid size),
+ * `repeats` timed runs each after one warm-up, and returns the fastest in
+ * `best` with its time.  Results are identical for every candidate, so only
+ * speed is compared.  The knobs in force are restored before returning; the
+ * caller applies `best` with gc_set_tuning.  (A library convenience, not in
+ * the paper.)
+ */
+gc_status gc_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64_t seed, gc_perm perm,
+                      int32_t iterations, int32_t repeats, gc_tuning* best, float* best_ms,
+                      void* stream);
+
 /* Number of kernel launches the library has made in this process. */
 int64_t gc_kernel_launches(void);
 

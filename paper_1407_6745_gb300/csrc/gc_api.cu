@@ -551,6 +551,70 @@ gc_status gc_get_tuning(gc_tuning* out) {
     return GC_OK;
 }
 
+gc_status gc_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64_t seed, gc_perm perm,
+                      int32_t iterations, int32_t repeats, gc_tuning* best, float* best_ms,
+                      void* stream) {
+    gc_status st = check_graph_args(g);
+    if (st != GC_OK) return st;
+    if (!best || g->mem != GC_MEM_DEVICE || repeats < 1 || g->n < 1) return GC_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    gc_tuning orig;
+    gc_get_tuning(&orig);
+    int32_t* colors = nullptr;
+    Scratch sc;
+    if (!sc.alloc(g->n * sizeof(int32_t), s)) return GC_ERR_OOM;
+    colors = sc.as<int32_t>();
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_it = [&](const gc_tuning& t, float* ms) -> gc_status {
+        gc_status r = gc_set_tuning(&t);
+        if (r != GC_OK) return r;
+        r = gc_color_recolor_impl(g, strategy, X, seed, perm, iterations, 0, colors, nullptr, nullptr,
+                                  nullptr, stream);  // warm-up
+        if (r != GC_OK) return r;
+        cudaEventRecord(e0, s);
+        for (int32_t i = 0; i < repeats && r == GC_OK; ++i)
+            r = gc_color_recolor_impl(g, strategy, X, seed, perm, iterations, 0, colors, nullptr,
+                                      nullptr, nullptr, stream);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float t_ms = 0.f;
+        cudaEventElapsedTime(&t_ms, e0, e1);
+        *ms = t_ms / repeats;
+        return r;
+    };
+    gc_tuning cur = orig;
+    float cur_ms = 0.f;
+    st = time_it(cur, &cur_ms);
+    // one knob at a time, keeping any improvement
+    const int32_t groups[][3] = {{64, 64, 64}, {4, 8, 16}, {0, 0, 0}, {0, 64, 64}, {16, 32, 64}};
+    const int32_t warp_max[] = {128, 512, 2048};
+    const int32_t blocks_per_sm[] = {0, 2, 4};
+    for (int step = 0; step < 5 && st == GC_OK; ++step) {
+        const int variants = step == 0 ? 5 : step == 1 ? 3 : step == 2 ? 2 : step == 3 ? 2 : 3;
+        for (int i = 0; i < variants && st == GC_OK; ++i) {
+            gc_tuning t = cur;
+            if (step == 0) { t.g4_max_deg = groups[i][0]; t.g8_max_deg = groups[i][1]; t.g16_max_deg = groups[i][2]; }
+            else if (step == 1) t.warp_max_deg = warp_max[i];
+            else if (step == 2) t.recolor_mode = i;
+            else if (step == 3) t.spec_graph = i;
+            else t.grid_blocks = blocks_per_sm[i] * sm_count();
+            if (std::memcmp(&t, &cur, sizeof(t)) == 0) continue;
+            float ms = 0.f;
+            st = time_it(t, &ms);
+            if (st == GC_OK && ms < cur_ms) { cur = t; cur_ms = ms; }
+        }
+    }
+    gc_set_tuning(&orig);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != GC_OK) return st;
+    *best = cur;
+    if (best_ms) *best_ms = cur_ms;
+    return GC_OK;
+}
+
 int64_t gc_kernel_launches(void) { return g_launches.load(); }
 
 const char* gc_status_string(gc_status s) {

@@ -85,3 +85,20 @@ def test_batch_host_memory_and_errors():
     with pytest.raises(gc.GCError) as e:
         gc.gc_recolor_batch(du.offsets, du.idx, desc, torch.ones(du.n, dtype=torch.int32, device="cuda"))
     assert e.value.name == "GC_ERR_IMPROPER_INPUT"
+
+
+def test_autotune_returns_valid_knobs_and_caches(tmp_path, monkeypatch):
+    from paper_1407_6745_gb300 import autotune
+    monkeypatch.setenv("GC_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    g = gg.workload("rmat12").to("cuda")
+    before = gc.gc_get_tuning()
+    knobs, ms = autotune.autotune(g.offsets, g.idx, "RXF", 4, 3, "RAND", 3)
+    assert ms > 0 and gc.gc_get_tuning() == before
+    ref, _ = gc.gc_color(g.offsets, g.idx, "RXF", 4, 3)
+    try:
+        applied = autotune.apply(g.offsets, g.idx, "RXF", 4, 3, "RAND", 3)
+        assert (tmp_path / "tune.json").exists() and gc.gc_get_tuning() == applied
+        again, _ = gc.gc_color(g.offsets, g.idx, "RXF", 4, 3)
+        assert torch.equal(ref, again)
+    finally:
+        gc.gc_set_tuning()
