@@ -210,6 +210,8 @@ def run_batch(args):
     t0 = time.perf_counter()
     graphs = gg.batch_mix(args.batch_count, 6, 1e3, args.batch_nmax, device=dev)
     union = gg.batch_union(graphs, device=dev)
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()  # generation temporaries back to the device
     gen_s = time.perf_counter() - t0
     desc = [dict(n=g.n, seed=1000 + i, X=4, perm="RV", iterations=5, perm_seed=0)
             for i, g in enumerate(graphs)]

@@ -62,11 +62,15 @@ void* scratch_alloc(size_t bytes, cudaStream_t s) {
     cudaMemPool_t p = pool_for_current_device();
     if (!p) return nullptr;
     void* ptr = nullptr;
-    if (cudaMallocFromPoolAsync(&ptr, bytes, p, s) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    return ptr;
+    if (cudaMallocFromPoolAsync(&ptr, bytes, p, s) == cudaSuccess) return ptr;
+    cudaGetLastError();
+    // The pool keeps freed memory for reuse; give it back to the device and
+    // try once more before reporting GC_ERR_OOM.
+    cudaStreamSynchronize(s);
+    cudaMemPoolTrimTo(p, 0);
+    if (cudaMallocFromPoolAsync(&ptr, bytes, p, s) == cudaSuccess) return ptr;
+    cudaGetLastError();
+    return nullptr;
 }
 
 void scratch_free(void* p, cudaStream_t s) { cudaFreeAsync(p, s); }
