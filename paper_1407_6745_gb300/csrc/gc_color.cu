@@ -578,7 +578,7 @@ gc_status batch_layout(const Graph& g, const gc_batch_graph* graphs, int32_t ng,
 gc_status batch_graph_of(const Graph& g, const BatchDesc* d_desc, int32_t ng, int32_t* graph_of,
                          cudaStream_t s) {
     if (g.n == 0) return GC_OK;
-    const int grid = static_cast<int>(std::min<int64_t>((g.n + kBlock - 1) / kBlock,
+    const int grid = static_cast<int>(std::min<int64_t>((static_cast<int64_t>(g.n) + kBlock - 1) / kBlock,
                                                         persistent_grid(current_tuning())));
     GC_LAUNCH(KID_BATCH, s, k_graph_of<<<grid, kBlock, 0, s>>>(g.n, d_desc, ng, graph_of));
     return GC_OK;
@@ -592,7 +592,7 @@ gc_status batch_max_colors(const Graph& g, const int32_t* graph_of, const int32_
     cudaMemsetAsync(sm.p, 0, ng * 4, s);
     cudaMemsetAsync(sr.p, 0, ng * 4, s);
     if (g.n > 0) {
-        const int grid = static_cast<int>(std::min<int64_t>((g.n + kBlock - 1) / kBlock,
+        const int grid = static_cast<int>(std::min<int64_t>((static_cast<int64_t>(g.n) + kBlock - 1) / kBlock,
                                                             persistent_grid(current_tuning())));
         GC_LAUNCH(KID_BATCH, s,
                   k_batch_stats<<<grid, kBlock, 0, s>>>(g.n, graph_of, colors, win_round,
@@ -614,8 +614,8 @@ gc_status color_batch_device(const Graph& g, const gc_batch_graph* graphs, int32
     if (st != GC_OK) return st;
     static_assert(sizeof(BatchDesc) == sizeof(gc_batch_graph), "descriptor layout");
     Scratch sd, sgo, swr;
-    if (!sd.alloc(static_cast<size_t>(ng) * sizeof(BatchDesc), s) || !sgo.alloc(g.n * 4 + 4, s) ||
-        !swr.alloc(g.n * 4 + 4, s))
+    if (!sd.alloc(static_cast<size_t>(ng) * sizeof(BatchDesc), s) || !sgo.alloc(static_cast<int64_t>(g.n) * 4 + 4, s) ||
+        !swr.alloc(static_cast<int64_t>(g.n) * 4 + 4, s))
         return GC_ERR_OOM;
     cudaError_t e = cudaMemcpyAsync(sd.p, graphs, static_cast<size_t>(ng) * sizeof(BatchDesc),
                                     cudaMemcpyHostToDevice, s);

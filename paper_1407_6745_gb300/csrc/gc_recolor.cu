@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
     __shared__ int32_t s_base[kScatterSegs];
     if (a.ctrl->err & (kErrImproper | kErrBadGraph)) return;
     const int32_t nseg = a.ctrl->k * kNB;
-    const int64_t chunk = (a.g.n + gridDim.x - 1) / gridDim.x;
+    const int64_t chunk = (static_cast<int64_t>(a.g.n) + gridDim.x - 1) / gridDim.x;
     const int64_t lo = blockIdx.x * chunk;
     const int64_t hi = a.g.n < lo + chunk ? a.g.n : lo + chunk;
     if (nseg > kScatterSegs) {

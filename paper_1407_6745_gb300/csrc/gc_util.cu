@@ -153,7 +153,7 @@ gc_status validate_device(const Graph& g, const int32_t* colors, gc_validation* 
     out->first_bad_vertex = -1;
     if (g.n == 0) return GC_OK;
     Scratch sc, sp, shv;
-    if (!sc.alloc(sizeof(ValCtrl), s) || !sp.alloc(kPresWords * 4, s) || !shv.alloc(g.n * 4, s))
+    if (!sc.alloc(sizeof(ValCtrl), s) || !sp.alloc(kPresWords * 4, s) || !shv.alloc(static_cast<int64_t>(g.n) * 4, s))
         return GC_ERR_OOM;
     ValArgs a{g, colors, sc.as<ValCtrl>(), sp.as<uint32_t>(), shv.as<int32_t>()};
     ValCtrl h;
@@ -179,7 +179,7 @@ gc_status validate_device(const Graph& g, const int32_t* colors, gc_validation* 
         if (!sb.alloc(words * 4, s)) return GC_ERR_OOM;
         cudaMemsetAsync(sb.p, 0, words * 4, s);
         cudaMemsetAsync(&a.c->distinct, 0, sizeof(unsigned long long), s);
-        const int vg = static_cast<int>(std::min<int64_t>((g.n + kBlock - 1) / kBlock, grid));
+        const int vg = static_cast<int>(std::min<int64_t>((static_cast<int64_t>(g.n) + kBlock - 1) / kBlock, grid));
         GC_LAUNCH(KID_MARK_PRESENT, s, k_mark_present<<<vg, kBlock, 0, s>>>(g.n, colors, sb.as<uint32_t>()));
         const int wg = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((words + kBlock - 1) / kBlock, grid)));
         GC_LAUNCH(KID_COUNT_BITS, s, k_count_bits<<<wg, kBlock, 0, s>>>(words, sb.as<uint32_t>(), a.c));
