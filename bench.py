@@ -51,6 +51,7 @@ WORKLOADS = {
                    label="R-MAT scale 24 ef 16 (0.57,0.19,0.19,0.05) seed 4; First Fit "
                          "+ 20 recoloring iterations RAND (seed 5)"),
     "batch": dict(label="batch"),
+    "serve": dict(label="serve"),
     "er10k": dict(graph="er10k", strategy="FF", X=1, seed=1, perm="RV", iterations=2, perm_seed=0,
                   label="Erdos-Renyi n=10,000 mean degree 16 (seed 1); First Fit + 2 iterations RV"),
 }
@@ -270,6 +271,173 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def serve_pool(count: int, seed: int, device):
+    """The served graph families: each drawn uniformly from G(n, p) (n
+    log-uniform in [1e3, 1e6], mean degree U[8, 32]), the 27-point stencil
+    (side U[16, 128]) and R-MAT (scale U[14, 22], edge factor 16,
+    (0.57, 0.19, 0.19, 0.05)); returned in pinned host memory."""
+    import math
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(count):
+        kind = int(rng.integers(0, 3))
+        if kind == 0:
+            n = int(round(math.exp(rng.uniform(math.log(1e3), math.log(1e6)))))
+            g = gg.erdos_renyi(n, float(rng.uniform(8.0, 32.0)), seed=seed * 1000 + i, device=device)
+            name = f"er n={n}"
+        elif kind == 1:
+            side = int(rng.integers(16, 129))
+            g = gg.stencil_3d(side, side, side, 27, device=device)
+            name = f"st27 side={side}"
+        else:
+            scale = int(rng.integers(14, 23))
+            g = gg.rmat(scale, 16, 0.57, 0.19, 0.19, seed=seed * 1000 + i, device=device)
+            name = f"rmat scale={scale}"
+        pool.append((name, g.offsets.cpu().pin_memory(), g.idx.cpu().pin_memory()))
+    return pool
+
+
+def serve_requests(pool, count: int, seed: int):
+    """Requests over the pool: a graph drawn uniformly, First Fit with its own
+    seed, k ~ U[1, 20] recoloring iterations, permutation uniform over
+    {RV, NI, RAND}."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        reqs.append(dict(graph=int(rng.integers(0, len(pool))), seed=int(rng.integers(0, 2**62)),
+                         iterations=int(rng.integers(1, 21)), perm=["RV", "NI", "RAND"][int(rng.integers(0, 3))],
+                         perm_seed=int(rng.integers(0, 2**32))))
+    return reqs
+
+
+def run_serve(args):
+    """Serving workload: a pool of graphs (serve_pool, seed 7) and a stream
+    of requests over it (serve_requests, seed 7).  Capacity = graphs/s with
+    every request submitted at once (the server batching as it likes);
+    one-by-one = a gc_color_recolor call per request from the same pinned host
+    buffers; then Poisson arrivals (seed 7) at `serve_load` x capacity, with
+    p50/p99 submit-to-result latency.  All three run end to end: graphs in
+    pinned host memory, colors back in host memory."""
+    import threading
+    import paper_1407_6745_gb300 as gc
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    gc.load()
+    t0 = time.perf_counter()
+    pool = serve_pool(args.serve_pool, 7, dev)
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
+    gen_s = time.perf_counter() - t0
+    reqs = serve_requests(pool, args.serve_requests, 7)
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(free * 0.6)
+
+    def submit(srv, r):
+        _, off, idx = pool[r["graph"]]
+        return gc.gc_server_submit(srv, off, idx, "FF", 1, r["seed"], r["perm"], r["iterations"],
+                                   r["perm_seed"])
+
+    def burst(reqs_, max_batch, workers):
+        with gc.gc_server_create(budget, max_batch, workers) as srv:
+            ts = [submit(srv, r) for r in reqs_]
+            res = [gc.gc_server_wait(srv, t) for t in ts]
+            info = gc.gc_server_stats(srv)
+        return res, info
+
+    # warm-up: every graph of the pool once, through the server
+    burst([dict(graph=i, seed=1, iterations=1, perm="RV", perm_seed=0) for i in range(len(pool))],
+          args.serve_batch, args.serve_workers)
+    launches0 = gc.gc_kernel_launches()
+    with Clocks(0) as clk:
+        res, info = burst(reqs, args.serve_batch, args.serve_workers)
+    capacity = info["graphs_per_s"]
+    launches = gc.gc_kernel_launches() - launches0
+
+    # one graph at a time, same host buffers
+    outs = {}
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        _, off, idx = pool[r["graph"]]
+        col, nc, st, _ = gc.gc_color_recolor(off, idx, "FF", 1, r["seed"], r["perm"], r["iterations"],
+                                             r["perm_seed"])
+        if i < args.serve_check:
+            outs[i] = (col, nc[-1], st["rounds"])
+    single_s = time.perf_counter() - t1
+    single_gps = len(reqs) / single_s
+    parity = all(torch.equal(res[i][0], outs[i][0]) and res[i][1]["max_color"] == outs[i][1]
+                 and res[i][1]["rounds"] == outs[i][2] for i in outs)
+
+    # Poisson arrivals at serve_load x capacity
+    rate = args.serve_load * capacity
+    gaps = np.random.default_rng(7).exponential(1.0 / rate, size=len(reqs))
+    arrivals = np.cumsum(gaps)
+    with gc.gc_server_create(budget, args.serve_batch, args.serve_workers) as srv:
+        tickets = [None] * len(reqs)
+
+        def client():
+            start = time.perf_counter()
+            for i, r in enumerate(reqs):
+                delay = arrivals[i] - (time.perf_counter() - start)
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[i] = submit(srv, r)
+
+        th = threading.Thread(target=client)
+        th.start()
+        th.join()
+        pres = [gc.gc_server_wait(srv, t) for t in tickets]
+        pinfo = gc.gc_server_stats(srv)
+    ppar = all(torch.equal(pres[i][0], res[i][0]) for i in range(len(reqs)))
+    batch_sizes = [p[1]["batch_size"] for p in pres]
+
+    # the oracle on the two smallest requests
+    import oracle
+    small = sorted(range(len(reqs)), key=lambda i: pool[reqs[i]["graph"]][1].numel())[:2]
+    oracle_ok = True
+    for i in small:
+        r = reqs[i]
+        _, off, idx = pool[r["graph"]]
+        oc, _ = oracle.color(off.numpy(), idx.numpy(), 1, r["seed"])
+        orc, _ = oracle.recolor(off.numpy(), idx.numpy(), oc, r["perm"], r["iterations"], r["perm_seed"])
+        oracle_ok &= bool(np.array_equal(res[i][0].numpy(), orc))
+
+    n_tot = sum(pool[r["graph"]][1].numel() - 1 for r in reqs)
+    nnz_tot = sum(pool[r["graph"]][2].numel() for r in reqs)
+    passes = sum(pool[r["graph"]][2].numel() * (1 + r["iterations"]) for r in reqs)
+    line = {"metric": "served graphs/s (e2e, saturated) vs one-by-one; p50/p99 latency at "
+                      f"{args.serve_load:g} x capacity",
+            "value": capacity, "unit": "graphs/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * len(reqs) / capacity, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"{len(reqs)} requests over a pool of {len(pool)} graphs: G(n,p) n "
+                                   "log-uniform [1e3,1e6] mean degree U[8,32] / 27-pt stencil side "
+                                   "U[16,128] / R-MAT scale U[14,22] ef 16, uniform; First Fit + "
+                                   "k~U[1,20] recoloring iterations, perm uniform {RV,NI,RAND}; seed 7",
+                       "requests": len(reqs), "pool": len(pool), "total_n": n_tot, "total_nnz": nnz_tot,
+                       "edge_passes": passes, "max_batch": args.serve_batch,
+                       "workers": args.serve_workers, "mem_budget_bytes": budget,
+                       "generation_s": round(gen_s, 1),
+                       "l2": "graphs from pinned host memory; most inputs larger than L2"},
+            "saturated": {"graphs_per_s": capacity, "gteps": passes / (len(reqs) / capacity) / 1e9,
+                          "p50_ms": info["p50_ms"], "p99_ms": info["p99_ms"], "batches": info["batches"]},
+            "one_by_one": {"graphs_per_s": single_gps, "s": single_s},
+            "speedup_vs_one_by_one": capacity / single_gps,
+            "poisson": {"rate_graphs_per_s": rate, "load": args.serve_load,
+                        "graphs_per_s": pinfo["graphs_per_s"], "p50_ms": pinfo["p50_ms"],
+                        "p99_ms": pinfo["p99_ms"], "mean_ms": pinfo["mean_ms"],
+                        "batches": pinfo["batches"], "mean_batch": float(np.mean(batch_sizes)),
+                        "max_batch_seen": int(max(batch_sizes)), "peak_bytes": pinfo["bytes_peak"]},
+            "parity": {f"served_equals_alone_first_{len(outs)}": parity,
+                       "poisson_equals_saturated_all": ppar, "oracle_on_2_smallest": oracle_ok},
+            "e2e": {"value": capacity, "unit": "graphs/s",
+                    "h2d_bytes_per_step": int(sum(8 * (pool[r["graph"]][1].numel()) + 4 * pool[r["graph"]][2].numel()
+                                                  for r in reqs)),
+                    "d2h_bytes_per_step": int(4 * n_tot)},
+            "clocks": clk.summary(), "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -281,9 +449,18 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-nmax", type=float, default=1e6)
+    ap.add_argument("--serve-pool", type=int, default=36)
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-batch", type=int, default=64)
+    ap.add_argument("--serve-workers", type=int, default=2)
+    ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--serve-check", type=int, default=40)
     args = ap.parse_args()
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     wl = WORKLOADS[args.workload]
     ws, rank, local = _dist()

@@ -70,9 +70,11 @@ typedef enum {
     GC_ERR_OOM = 4,            /* device or pinned host allocation failed    */
     GC_ERR_CUDA = 5,           /* a CUDA runtime call failed                 */
     GC_ERR_TIMEOUT = 6,        /* a bounded device-side wait ran out         */
-    GC_ERR_ROUND_LIMIT = 7     /* more than n+1 speculative rounds (cannot happen
+    GC_ERR_ROUND_LIMIT = 7,    /* more than n+1 speculative rounds (cannot happen
                                   for a valid graph: the top-priority vertex of the
                                   work set always keeps its color)           */
+    GC_ERR_BUDGET = 8,         /* a server request larger than its memory budget */
+    GC_PENDING = 9             /* a server request not finished yet (not an error) */
 } gc_status;
 
 typedef enum { GC_FIRST_FIT = 0, GC_RANDOM_X_FIT = 1 } gc_strategy;
@@ -206,6 +208,83 @@ gc_status gc_recolor_batch(const gc_graph* g, const gc_batch_graph* graphs, int3
 gc_status gc_color_recolor_batch(const gc_graph* g, const gc_batch_graph* graphs, int32_t ngraphs,
                                  int32_t* colors_out, int32_t* rounds_out, int32_t* max_color_out,
                                  gc_stats* stats, void* stream);
+
+/*
+ * Serving: a request loop that colors graphs as they arrive (a library
+ * extension, not in the paper).  Submitted requests are queued and admitted
+ * first come first served while they fit the device-memory budget and the
+ * batch limit; an admitted batch is laid out as one concatenated CSR on the
+ * device and colored plus recolored with the batch pipeline, its CSR, colors
+ * and work lists resident on the device across all its recoloring
+ * iterations.  Several workers (one CUDA stream each) run batches at the same
+ * time, so requests that arrive while a batch is on the GPU are admitted into
+ * the next one as soon as a worker and memory are free, and the batches
+ * overlap on the device.  Every request gets exactly the colors, round count
+ * and final max color that gc_color_recolor gives it alone.
+ */
+typedef struct gc_server gc_server;
+
+typedef struct {
+    gc_graph graph;      /* host or device memory; copied by gc_server_submit */
+    int32_t strategy;    /* gc_strategy */
+    int32_t X;           /* Random-X Fit's X (>= 1); ignored for First Fit */
+    uint64_t seed;
+    int32_t perm;        /* gc_perm */
+    int32_t iterations;
+    uint64_t perm_seed;
+} gc_request;
+
+typedef struct {
+    int32_t status;      /* gc_status of the request */
+    int32_t rounds;      /* speculative rounds */
+    int32_t max_color;   /* after the last recoloring iteration */
+    int32_t batch_size;  /* requests in its batch */
+    double submit_ms;    /* server clock (ms since gc_server_create) */
+    double start_ms;     /* its batch started */
+    double done_ms;      /* result available */
+} gc_request_result;
+
+typedef struct {
+    int64_t submitted, completed, rejected, batches;
+    double p50_ms, p99_ms, mean_ms;  /* submit-to-done latency, completed requests */
+    double graphs_per_s;             /* completed / (last done - first submit)     */
+    int64_t bytes_in_use, bytes_peak;/* admitted device-memory estimate            */
+} gc_server_info;
+
+/* Starts a server on the calling thread's current CUDA device.
+ * mem_budget: bytes of device memory the admitted requests may hold at once
+ *   (an estimate per request: its CSR and colors plus the larger of the
+ *   coloring and the recoloring scratch);
+ * max_batch: requests per batch (1..65535); workers: concurrent batches, one
+ *   host thread and CUDA stream each (1..64).  With workers > 1 the
+ *   recoloring runs stepwise (gc_tuning.recolor_mode = 1), since concurrent
+ *   batches share the SMs; otherwise the tuning in force at creation is used.
+ * Errors: GC_ERR_INVALID_ARG, GC_ERR_CUDA (no usable device).
+ * Every gc_server_* call is thread-safe. */
+gc_status gc_server_create(size_t mem_budget, int32_t max_batch, int32_t workers, gc_server** out);
+/* Queues a request; *ticket identifies it.  The graph is NOT copied: its
+ * offsets and ids (host memory -- pinned memory uploads fastest -- or device
+ * memory, complete before the call) must stay valid and unchanged until the
+ * request's result has been claimed or the server destroyed.  The offsets are
+ * checked here, the ids when its batch is staged on the device.  Errors, with
+ * nothing queued: GC_ERR_INVALID_ARG, GC_ERR_BAD_GRAPH (offsets),
+ * GC_ERR_BUDGET (its estimate exceeds mem_budget), GC_ERR_CUDA (reading
+ * device offsets).  A request whose ids are malformed finishes with
+ * GC_ERR_BAD_GRAPH.  A graph without vertices finishes at once. */
+gc_status gc_server_submit(gc_server* s, const gc_request* r, uint64_t* ticket);
+/* GC_PENDING while queued or running.  Otherwise returns the request's status
+ * and fills colors_out (host, n entries; may be NULL; written only for GC_OK)
+ * and res (may be NULL); the server then forgets the ticket, so a second
+ * poll or wait on it returns GC_ERR_INVALID_ARG (as does an unknown ticket). */
+gc_status gc_server_poll(gc_server* s, uint64_t ticket, int32_t* colors_out, gc_request_result* res);
+/* As gc_server_poll, blocking up to timeout_ms (< 0: until it finishes). */
+gc_status gc_server_wait(gc_server* s, uint64_t ticket, int32_t* colors_out, gc_request_result* res,
+                         int32_t timeout_ms);
+/* Counters and latency percentiles (nearest rank) since creation. */
+gc_status gc_server_stats(gc_server* s, gc_server_info* out);
+/* Finishes the queued requests, stops the workers and frees the server with
+ * any results not yet claimed. */
+void gc_server_destroy(gc_server* s);
 
 /* Checks the coloring against the definition of Sec. 1 and the graph's
  * structure (GC_ERR_BAD_GRAPH if malformed). */

@@ -22,7 +22,8 @@ __all__ = [
     "GCError", "FIRST_FIT", "RANDOM_X_FIT", "PERM", "library_path", "load",
     "gc_color", "gc_recolor", "gc_color_recolor", "gc_color_batch", "gc_recolor_batch",
     "gc_color_recolor_batch", "gc_validate", "gc_validate_noalloc",
-    "gc_check_graph",
+    "gc_check_graph", "gc_server_create", "gc_server_submit", "gc_server_poll", "gc_server_wait",
+    "gc_server_stats", "gc_server_destroy",
     "gc_priorities", "gc_set_tuning", "gc_get_tuning", "gc_profile_enable", "gc_profile_read",
     "gc_kernel_launches", "gc_status_string", "gc_version",
 ]
@@ -36,7 +37,8 @@ FIRST_FIT, RANDOM_X_FIT = 0, 1
 PERM = {"RV": 0, "NI": 1, "ND": 2, "RAND": 3}
 GC_MEM_DEVICE, GC_MEM_HOST = 0, 1
 STATUS = {0: "GC_OK", 1: "GC_ERR_INVALID_ARG", 2: "GC_ERR_BAD_GRAPH", 3: "GC_ERR_IMPROPER_INPUT",
-          4: "GC_ERR_OOM", 5: "GC_ERR_CUDA", 6: "GC_ERR_TIMEOUT", 7: "GC_ERR_ROUND_LIMIT"}
+          4: "GC_ERR_OOM", 5: "GC_ERR_CUDA", 6: "GC_ERR_TIMEOUT", 7: "GC_ERR_ROUND_LIMIT",
+          8: "GC_ERR_BUDGET", 9: "GC_PENDING"}
 
 
 class GCError(RuntimeError):
@@ -80,6 +82,26 @@ class _Tuning(ctypes.Structure):
                                                "spin_limit", "spec_graph")]
 
 
+class _Request(ctypes.Structure):
+    _fields_ = [("graph", _Graph), ("strategy", ctypes.c_int32), ("X", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("perm", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("perm_seed", ctypes.c_uint64)]
+
+
+class _RequestResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("rounds", ctypes.c_int32), ("max_color", ctypes.c_int32),
+                ("batch_size", ctypes.c_int32), ("submit_ms", ctypes.c_double),
+                ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+
+
+class _ServerInfo(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("graphs_per_s", ctypes.c_double), ("bytes_in_use", ctypes.c_int64),
+                ("bytes_peak", ctypes.c_int64)]
+
+
 def library_path() -> str:
     return _LIB_PATH
 
@@ -117,9 +139,20 @@ def load():
         lib.gc_priorities.restype = ctypes.c_int
         lib.gc_set_tuning.argtypes = [ctypes.POINTER(_Tuning)]
         lib.gc_get_tuning.argtypes = [ctypes.POINTER(_Tuning)]
+        H = ctypes.c_void_p
+        lib.gc_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(H)]
+        lib.gc_server_submit.argtypes = [H, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)]
+        lib.gc_server_poll.argtypes = [H, ctypes.c_uint64, P, ctypes.POINTER(_RequestResult)]
+        lib.gc_server_wait.argtypes = [H, ctypes.c_uint64, P, ctypes.POINTER(_RequestResult),
+                                       ctypes.c_int32]
+        lib.gc_server_stats.argtypes = [H, ctypes.POINTER(_ServerInfo)]
+        lib.gc_server_destroy.argtypes = [H]
+        lib.gc_server_destroy.restype = None
         for f in ("gc_color", "gc_recolor", "gc_color_recolor", "gc_validate", "gc_validate_noalloc",
-    "gc_check_graph",
-                  "gc_priorities", "gc_set_tuning", "gc_get_tuning"):
+                  "gc_check_graph", "gc_priorities", "gc_set_tuning", "gc_get_tuning",
+                  "gc_server_create", "gc_server_submit", "gc_server_poll", "gc_server_wait",
+                  "gc_server_stats"):
             getattr(lib, f).restype = ctypes.c_int
         lib.gc_kernel_launches.restype = ctypes.c_int64
         lib.gc_profile_enable.argtypes = [ctypes.c_int32]
@@ -350,6 +383,105 @@ def gc_priorities(seed: int, n: int, device="cuda", stream=None):
     _check(lib.gc_priorities(int(seed) & (2**64 - 1), int(n), _ptr(out), _stream(dev, stream)),
            "gc_priorities")
     return out.to(torch.int64) & 0xFFFFFFFF
+
+
+GC_PENDING = 9
+
+
+class GCServer:
+    """Handle of a gc_server (the serving loop); use the gc_server_* functions.
+    Holds each pending request's graph tensors (the server reads them in
+    place) and vertex count until its result is claimed."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.pending = {}
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        gc_server_destroy(self)
+
+
+def gc_server_create(mem_budget: int, max_batch: int = 64, workers: int = 2) -> GCServer:
+    """Start a server on the current CUDA device: admission by a device-memory
+    budget (bytes), batches of at most max_batch requests, `workers`
+    concurrent batches."""
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib.gc_server_create(int(mem_budget), int(max_batch), int(workers), ctypes.byref(h)),
+           "gc_server_create")
+    return GCServer(h)
+
+
+def gc_server_submit(server: GCServer, offsets, idx, strategy="FF", X: int = 1, seed: int = 0,
+                     perm="RV", iterations: int = 0, perm_seed: int = 0) -> int:
+    """Queue one request; returns its ticket.  The tensors are kept alive by
+    the handle until the result is claimed (the server reads them in place);
+    do not modify them meanwhile."""
+    lib = load()
+    g, keep = _graph(offsets, idx)
+    if keep[0].is_cuda:
+        torch.cuda.current_stream(keep[0].device).synchronize()
+    q = _Request()
+    q.graph = g
+    q.strategy = _strategy(strategy)
+    q.X = int(X)
+    q.seed = int(seed) & (2**64 - 1)
+    q.perm = _perm(perm)
+    q.iterations = int(iterations)
+    q.perm_seed = int(perm_seed) & (2**64 - 1)
+    t = ctypes.c_uint64()
+    _check(lib.gc_server_submit(server.handle, ctypes.byref(q), ctypes.byref(t)), "gc_server_submit")
+    server.pending[t.value] = (g.n, keep)
+    return t.value
+
+
+def _server_result(server, ticket, rc, out, res, where):
+    if rc == GC_PENDING:
+        return None
+    server.pending.pop(ticket, None)
+    _check(rc, where)
+    return out, {k: getattr(res, k) for k, _ in _RequestResult._fields_}
+
+
+def gc_server_poll(server: GCServer, ticket: int):
+    """None while pending, else (colors int32[n] on the CPU, result dict);
+    raises GCError if the request failed.  A result is handed out once."""
+    lib = load()
+    n = server.pending.get(ticket, (0, None))[0]
+    out = torch.empty(n, dtype=torch.int32)
+    res = _RequestResult()
+    rc = lib.gc_server_poll(server.handle, ctypes.c_uint64(ticket), _ptr(out), ctypes.byref(res))
+    return _server_result(server, ticket, rc, out, res, "gc_server_poll")
+
+
+def gc_server_wait(server: GCServer, ticket: int, timeout_ms: int = -1):
+    """As gc_server_poll, blocking up to timeout_ms (< 0: until done)."""
+    lib = load()
+    n = server.pending.get(ticket, (0, None))[0]
+    out = torch.empty(n, dtype=torch.int32)
+    res = _RequestResult()
+    rc = lib.gc_server_wait(server.handle, ctypes.c_uint64(ticket), _ptr(out), ctypes.byref(res),
+                            int(timeout_ms))
+    return _server_result(server, ticket, rc, out, res, "gc_server_wait")
+
+
+def gc_server_stats(server: GCServer):
+    """Counts, p50/p99/mean submit-to-done latency (ms), graphs/s, memory in use."""
+    lib = load()
+    info = _ServerInfo()
+    _check(lib.gc_server_stats(server.handle, ctypes.byref(info)), "gc_server_stats")
+    return {k: getattr(info, k) for k, _ in _ServerInfo._fields_}
+
+
+def gc_server_destroy(server: GCServer):
+    """Finish the queued requests, stop the workers and free the server."""
+    if server.handle:
+        load().gc_server_destroy(server.handle)
+        server.handle = None
+        server.pending.clear()
 
 
 def gc_set_tuning(**knobs):

@@ -171,7 +171,18 @@ void prof_collect() {
     t_pending.clear();
 }
 
+namespace {
+thread_local bool t_tune_set = false;
+thread_local Tuning t_tune;
+}  // namespace
+
+void set_thread_tuning(const Tuning* t) {
+    t_tune_set = t != nullptr;
+    if (t) t_tune = *t;
+}
+
 Tuning current_tuning() {
+    if (t_tune_set) return t_tune;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     return g_tune;
 }
@@ -631,6 +642,8 @@ const char* gc_status_string(gc_status s) {
     case GC_ERR_CUDA: return "CUDA runtime error";
     case GC_ERR_TIMEOUT: return "bounded device wait expired";
     case GC_ERR_ROUND_LIMIT: return "speculative round limit exceeded";
+    case GC_ERR_BUDGET: return "request larger than the server's memory budget";
+    case GC_PENDING: return "request pending";
     }
     return "unknown status";
 }

@@ -56,8 +56,11 @@ void prof_collect();
         ::gc::note_launches(1);                   \
     } while (0)
 
-// The tuning in force (set with gc_set_tuning).
+// The tuning in force: the calling thread's own (set_thread_tuning), else the
+// process-wide one (gc_set_tuning).
 Tuning current_tuning();
+// Gives the calling thread its own tuning (nullptr: back to the process-wide one).
+void set_thread_tuning(const Tuning* t);
 
 gc_status cuda_status(cudaError_t e);
 gc_status status_from_err_bits(uint32_t bits);
@@ -76,6 +79,10 @@ struct Scratch {
         return p != nullptr;
     }
     template <class T> T* as() const { return static_cast<T*>(p); }
+    void reset() {
+        if (p) scratch_free(p, s);
+        p = nullptr;
+    }
 };
 
 // Speculative coloring on device pointers; writes colors_out (device) and,

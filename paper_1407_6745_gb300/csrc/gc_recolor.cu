@@ -927,7 +927,8 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
             if (ce != cudaSuccess) { st = cuda_status(ce); break; }
             tp.resize(static_cast<size_t>(hc.k) * kNB + 1);
-            ce = cudaMemcpy(tp.data(), a.tile_prefix, tp.size() * 4, cudaMemcpyDeviceToHost);
+            ce = cudaMemcpyAsync(tp.data(), a.tile_prefix, tp.size() * 4, cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
             if (ce != cudaSuccess) { st = cuda_status(ce); break; }
             for (int32_t p = 0; p < hc.k; ++p) {
                 const int32_t t0 = tp[p * kNB], t1 = tp[(p + 1) * kNB];
@@ -1106,7 +1107,8 @@ static gc_status recolor_batch_impl(const Graph& g, const gc_batch_graph* graphs
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
             if (ce != cudaSuccess) { st = cuda_status(ce); break; }
             tp.resize(static_cast<size_t>(hc.k) * kNB + 1);
-            ce = cudaMemcpy(tp.data(), a.tile_prefix, tp.size() * 4, cudaMemcpyDeviceToHost);
+            ce = cudaMemcpyAsync(tp.data(), a.tile_prefix, tp.size() * 4, cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
             if (ce != cudaSuccess) { st = cuda_status(ce); break; }
             for (int32_t p = 0; p < hc.k; ++p) {
                 const int32_t t0 = tp[p * kNB], t1 = tp[(p + 1) * kNB];

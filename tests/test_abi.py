@@ -59,3 +59,16 @@ def test_argument_checks_need_no_gpu():
         gc.gc_set_tuning(g4_max_deg=9, g8_max_deg=8)
     gc.gc_set_tuning()
     assert gc.gc_get_tuning()["warp_max_deg"] == 512
+    for budget, max_batch, workers in ((0, 8, 2), (1 << 20, 0, 2), (1 << 20, 70000, 2), (1 << 20, 8, 0)):
+        with pytest.raises(gc.GCError) as e:
+            gc.gc_server_create(budget, max_batch, workers)
+        assert e.value.name == "GC_ERR_INVALID_ARG"
+
+
+def test_server_struct_layouts():
+    """The binding's ctypes structs match the header's field order and sizes."""
+    import ctypes
+    import paper_1407_6745_gb300 as gc
+    assert ctypes.sizeof(gc._Request) == 40 + 4 + 4 + 8 + 4 + 4 + 8
+    assert ctypes.sizeof(gc._RequestResult) == 4 * 4 + 3 * 8
+    assert ctypes.sizeof(gc._ServerInfo) == 4 * 8 + 4 * 8 + 2 * 8
