@@ -17,6 +17,14 @@
 // fixed in round 0 (a loser stays in its bucket, so a region never
 // overflows).  All per-round state (round number, bucket counts) lives in a
 // small device control block, so a round's two launches take no host input.
+//
+// Heavy rows (the block-per-row bucket) are not re-read every round: such a
+// vertex keeps a pending list of its neighbors that were still uncolored at
+// its last look and a bitmap of the colors of the others.  In each round it
+// folds the neighbors colored since then into the bitmap and drops them from
+// the list, so a round reads only the list; its conflicts can only be with
+// the list (a colored neighbor's color is forbidden to it).  The forbidden
+// set and the conflict candidates are exactly those of a full row scan.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -38,6 +46,8 @@ struct SpecCtrl {
     uint32_t done_blocks;
     unsigned long long edges;
     unsigned long long conflicts;
+    long long heavy_entries;  // pending-list entries over all heavy rows
+    long long heavy_words;    // bitmap words over all heavy rows
 };
 
 struct SpecArgs {
@@ -59,7 +69,19 @@ struct SpecArgs {
     const int32_t* graph_of;
     const BatchDesc* desc;
     int32_t* win_round;
+    // heavy rows (bucket 0): index of each, its pending list (start, length;
+    // length -1 until first built: the row itself) and forbidden bitmap
+    int32_t* hid;
+    int64_t* h_pbeg;
+    int32_t* h_pcnt;
+    int64_t* h_bbeg;
+    int32_t* h_bwords;
+    int32_t* pend;
+    uint32_t* hbm;
 };
+
+// Bitmap words of a heavy row: colors 1 .. 32 * words, at least deg + 64.
+__host__ __device__ __forceinline__ int32_t heavy_words(int32_t deg) { return (deg + 64) / 32 + 2; }
 
 // Random-X index of v in `round`: the graph's own seed, X and local id.
 __device__ __forceinline__ uint32_t draw_index(const SpecArgs& a, int32_t v, int32_t round) {
@@ -135,6 +157,72 @@ __global__ void __launch_bounds__(kBlock) k_spec_fill(SpecArgs a) {
     }
 }
 
+// Heavy rows: index, pending-list and bitmap offsets (exclusive scans over
+// the bucket-0 region of the round-0 list), one block.
+constexpr int kHeavyThreads = 1024;
+__global__ void __launch_bounds__(kHeavyThreads) k_heavy_setup(SpecArgs a, int32_t nh) {
+    __shared__ long long s_e[kHeavyThreads / 32], s_w[kHeavyThreads / 32];
+    __shared__ long long s_base_e, s_base_w;
+    const int l = lane_id(), w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        s_base_e = 0;
+        s_base_w = 0;
+    }
+    __syncthreads();
+    const int32_t start0 = a.ctrl->start[0];
+    for (int32_t h0 = 0; h0 < nh; h0 += kHeavyThreads) {
+        const int32_t h = h0 + static_cast<int32_t>(threadIdx.x);
+        long long e = 0, wd = 0;
+        int32_t v = 0;
+        if (h < nh) {
+            const WorkItem it = load_item(a.list0 + start0 + h);
+            v = it.v;
+            e = it.deg;
+            wd = heavy_words(it.deg);
+        }
+        long long ie = e, iw = wd;  // warp inclusive scans
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const long long ye = __shfl_up_sync(kFull, ie, d), yw = __shfl_up_sync(kFull, iw, d);
+            if (l >= d) {
+                ie += ye;
+                iw += yw;
+            }
+        }
+        if (l == 31) {
+            s_e[w] = ie;
+            s_w[w] = iw;
+        }
+        __syncthreads();
+        long long be = s_base_e, bw = s_base_w, te = 0, tw = 0;
+        for (int k = 0; k < kHeavyThreads / 32; ++k) {
+            if (k < w) {
+                be += s_e[k];
+                bw += s_w[k];
+            }
+            te += s_e[k];
+            tw += s_w[k];
+        }
+        if (h < nh) {
+            a.hid[v] = h;
+            a.h_pbeg[h] = be + ie - e;
+            a.h_pcnt[h] = -1;
+            a.h_bbeg[h] = bw + iw - wd;
+            a.h_bwords[h] = static_cast<int32_t>(wd);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_base_e += te;
+            s_base_w += tw;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.ctrl->heavy_entries = s_base_e;
+        a.ctrl->heavy_words = s_base_w;
+    }
+}
+
 // Tile bookkeeping of one round, loaded by every block at kernel start.
 struct RoundTiles {
     int32_t cnt[kNB];
@@ -202,6 +290,83 @@ __device__ __forceinline__ void tentative_group_tile(const SpecArgs& a, const Ro
     }
 }
 
+// Heavy row v in round >= 1 (the whole block): folds the neighbors colored
+// since v's last look into its bitmap, keeps the uncolored ones in its
+// pending list (compacted in place: a kept id moves to a position at or
+// below the one it was read from, after the whole chunk has been read), then
+// takes the j-th permissible color from the bitmap.  Past the bitmap's free
+// colors (Random-X with a large X) the row is scanned in full instead.
+__device__ int32_t choose_heavy(const SpecArgs& a, const WorkItem& it, uint32_t j, SpecShared& sm) {
+    const int t = threadIdx.x, l = lane_id(), w = t >> 5;
+    const int32_t h = a.hid[it.v];
+    const int32_t pc = a.h_pcnt[h];
+    const int64_t cnt = pc < 0 ? static_cast<int64_t>(it.deg) : static_cast<int64_t>(pc);
+    const int32_t* src = pc < 0 ? a.g.idx + it.beg : a.pend + a.h_pbeg[h];
+    int32_t* dst = a.pend + a.h_pbeg[h];
+    uint32_t* bm = a.hbm + a.h_bbeg[h];
+    const int32_t words = a.h_bwords[h];
+    const uint32_t bits = 32u * static_cast<uint32_t>(words);
+    int32_t kept = 0;
+    for (int64_t i0 = 0; i0 < cnt; i0 += kBlock) {
+        const int64_t i = i0 + t;
+        int32_t u = 0;
+        bool keep = false;
+        if (i < cnt) {
+            u = src[i];
+            if (u < 0 || u >= a.g.n) {
+                atomicOr(&a.ctrl->err, kErrBadGraph);
+            } else {
+                const int32_t c = __ldg(a.color + u);
+                if (c == 0) keep = true;
+                else if (static_cast<uint32_t>(c - 1) < bits)
+                    atomicOr(bm + ((c - 1) >> 5), 1u << ((c - 1) & 31));
+            }
+        }
+        const unsigned bal = __ballot_sync(kFull, keep);
+        if (l == 0) sm.blk.wsum[w] = static_cast<uint32_t>(__popc(bal));
+        __syncthreads();
+        int32_t before = 0, total = 0;
+#pragma unroll
+        for (int k = 0; k < kWarps; ++k) {
+            const int32_t x = static_cast<int32_t>(sm.blk.wsum[k]);
+            if (k < w) before += x;
+            total += x;
+        }
+        if (keep) dst[kept + before + __popc(bal & ((1u << l) - 1u))] = u;
+        kept += total;
+        __syncthreads();
+    }
+    if (t == 0) a.h_pcnt[h] = kept;
+    // the j-th free bit of the bitmap (bit b = color b + 1); L2 reads, since
+    // the block's own atomics went there
+    for (int32_t w0 = 0; w0 < words; w0 += kBlock) {
+        const int32_t wi = w0 + t;
+        const uint32_t f = wi < words ? ~__ldcg(bm + wi) : 0u;
+        const uint32_t cnt_f = static_cast<uint32_t>(__popc(f));
+        const uint32_t incl_w = warp_inclusive_scan(cnt_f);
+        if (l == 31) sm.blk.wsum[w] = incl_w;
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+#pragma unroll
+        for (int k = 0; k < kWarps; ++k) {
+            const uint32_t x = sm.blk.wsum[k];
+            if (k < w) before += x;
+            total += x;
+        }
+        const uint32_t incl = incl_w + before, excl = incl - cnt_f;
+        if (j < total) {
+            if (j >= excl && j < incl) sm.blk.result = 32 * wi + select_bit32(f, j - excl) + 1;
+            __syncthreads();
+            const int32_t color = sm.blk.result;
+            __syncthreads();
+            return color;
+        }
+        j -= total;
+        __syncthreads();
+    }
+    return -1;  // past the bitmap
+}
+
 template <bool kRXF>
 __global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
     __shared__ SpecShared sm;
@@ -220,7 +385,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
         case 0: {
             const WorkItem it = load_item(list + rt.start[0] + first);
             const uint32_t j = kRXF ? draw_index(a, it.v, round) : 0u;
-            const int32_t c = choose_block<4>(a.g, it.beg, it.deg, j, fetch, sm.blk, &a.ctrl->err);
+            // round 0: nothing is colored yet, so the j-th permissible color is j + 1
+            int32_t c = round == 0 ? static_cast<int32_t>(j) + 1 : choose_heavy(a, it, j, sm);
+            if (c < 0) c = choose_block<4>(a.g, it.beg, it.deg, j, fetch, sm.blk, &a.ctrl->err);
             if (threadIdx.x == 0) {
                 set_tent(a, it.v, c);
                 edges += static_cast<unsigned long long>(it.deg);
@@ -275,6 +442,30 @@ __device__ __forceinline__ bool loses(const SpecArgs& a, const WorkItem& it, int
     return lose;
 }
 
+// The same test for a heavy row after round 0, over its pending list: the
+// neighbors uncolored before the round, the only ones that can share its
+// tentative color.
+__device__ __forceinline__ bool loses_pending(const SpecArgs& a, const WorkItem& it) {
+    const int32_t h = a.hid[it.v];
+    const int32_t pc = a.h_pcnt[h];
+    const int32_t* lst = a.pend + a.h_pbeg[h];
+    const unsigned long long* key = reinterpret_cast<const unsigned long long*>(a.key);
+    const uint64_t kv = __ldg(key + it.v);
+    const uint32_t tv = static_cast<uint32_t>(kv >> 32);
+    bool lose = false;
+    for (int32_t i = threadIdx.x; i < pc; i += kBlock) {
+        const int32_t u = __ldg(lst + i);
+        if (u < 0 || u >= a.g.n) {
+            atomicOr(&a.ctrl->err, kErrBadGraph);
+            continue;
+        }
+        const uint64_t ku = __ldg(key + u);
+        if (u != it.v && static_cast<uint32_t>(ku >> 32) == tv && (ku > kv || (ku == kv && u > it.v)))
+            lose = true;
+    }
+    return lose;
+}
+
 template <int G>
 __device__ __forceinline__ void conflict_group_tile(const SpecArgs& a, const RoundTiles& rt,
                                                     const WorkItem* list, WorkItem* next, int par,
@@ -315,7 +506,8 @@ __global__ void __launch_bounds__(kBlock) k_conflict(SpecArgs a) {
         switch (b) {
         case 0: {
             const WorkItem it = load_item(list + rt.start[0] + first);
-            const bool lose = __syncthreads_or(loses<1>(a, it, threadIdx.x, kBlock));
+            const bool mine = round == 0 ? loses<1>(a, it, threadIdx.x, kBlock) : loses_pending(a, it);
+            const bool lose = __syncthreads_or(mine);
             if (threadIdx.x == 0) {
                 edges += static_cast<unsigned long long>(it.deg);
                 if (lose) {
@@ -465,9 +657,18 @@ static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int3
     a.desc = desc;
     a.win_round = win_round;
 
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    struct Events {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        Events() {
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+        }
+        ~Events() {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+    } ev;
+    const cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     cudaEventRecord(e0, s);
     cudaMemsetAsync(a.ctrl, 0, sizeof(SpecCtrl), s);
     const int grid_t = resident_grid(X > 1 ? k_tentative<true> : k_tentative<false>, a.tune);
@@ -476,6 +677,38 @@ static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int3
         std::min<int64_t>((n + kBlock - 1) / kBlock, resident_grid(k_spec_setup, a.tune)));
     GC_LAUNCH(KID_SPEC_SETUP, s, k_spec_setup<<<setup_grid, kBlock, 0, s>>>(a));
     GC_LAUNCH(KID_SPEC_FILL, s, k_spec_fill<<<setup_grid, kBlock, 0, s>>>(a));
+    // heavy rows: their pending lists and bitmaps (sizes read back once)
+    Scratch sc_hid, sc_pbeg, sc_pcnt, sc_bbeg, sc_bwords, sc_pend, sc_hbm;
+    {
+        SpecCtrl h0;
+        cudaError_t ce = cudaMemcpyAsync(&h0, a.ctrl, sizeof(SpecCtrl), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) return cuda_status(ce);
+        if (h0.err) return status_from_err_bits(h0.err);
+        const int32_t nh = h0.init_cnt[0];
+        if (nh > 0) {
+            if (!sc_hid.alloc(n * 4, s) || !sc_pbeg.alloc(static_cast<int64_t>(nh) * 8, s) ||
+                !sc_pcnt.alloc(static_cast<int64_t>(nh) * 4, s) || !sc_bbeg.alloc(static_cast<int64_t>(nh) * 8, s) ||
+                !sc_bwords.alloc(static_cast<int64_t>(nh) * 4, s))
+                return GC_ERR_OOM;
+            a.hid = sc_hid.as<int32_t>();
+            a.h_pbeg = sc_pbeg.as<int64_t>();
+            a.h_pcnt = sc_pcnt.as<int32_t>();
+            a.h_bbeg = sc_bbeg.as<int64_t>();
+            a.h_bwords = sc_bwords.as<int32_t>();
+            GC_LAUNCH(KID_SPEC_FILL, s, k_heavy_setup<<<1, kHeavyThreads, 0, s>>>(a, nh));
+            ce = cudaMemcpyAsync(&h0, a.ctrl, sizeof(SpecCtrl), cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+            if (ce != cudaSuccess) return cuda_status(ce);
+            if (!sc_pend.alloc(static_cast<size_t>(h0.heavy_entries) * 4, s) ||
+                !sc_hbm.alloc(static_cast<size_t>(h0.heavy_words) * 4, s))
+                return GC_ERR_OOM;
+            a.pend = sc_pend.as<int32_t>();
+            a.hbm = sc_hbm.as<uint32_t>();
+            ce = cudaMemsetAsync(a.hbm, 0, static_cast<size_t>(h0.heavy_words) * 4, s);
+            if (ce != cudaSuccess) return cuda_status(ce);
+        }
+    }
     gc_status st = GC_OK;
     a.round_limit = static_cast<int32_t>(std::min<int64_t>(n + 2, INT32_MAX));
     if (a.tune.spec_graph) {
@@ -511,8 +744,6 @@ static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int3
         cudaEventElapsedTime(&ms, e0, e1);
         stats->ms_color = ms;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     return st;
 }
 
