@@ -9,7 +9,8 @@ The arithmetic lives in ``gc_oracle.c`` (plain single-threaded C, compiled
 with gcc into ``liboracle.so`` next to it); this module only marshals numpy
 arrays.  Passages followed: Alg. 1 and First Fit (Sec. 2.1), the speculative
 rounds of Sec. 2.2, Random-X Fit (Sec. 3.2), recoloring and the class
-permutations RV/NI/ND/RAND (Sec. 2.1, Sec. 3).  The readings taken where the
+permutations RV/NI/ND/RAND (Sec. 2.1, Sec. 3) and their ND-RAND schedules
+(Sec. 4.2.1).  The readings taken where the
 paper is silent are listed at the top of ``gc_oracle.c``.
 """
 from __future__ import annotations
@@ -31,6 +32,22 @@ OK, ERR_INVALID_ARG, ERR_BAD_GRAPH, ERR_IMPROPER_INPUT, ERR_OOM = 0, 1, 2, 3, 4
 ERR_ROUND_LIMIT = 7
 PERM_REVERSE, PERM_NONINC, PERM_NONDEC, PERM_RANDOM = 0, 1, 2, 3
 PERMS = {"RV": PERM_REVERSE, "NI": PERM_NONINC, "ND": PERM_NONDEC, "RAND": PERM_RANDOM}
+SCHED_POW2, SCHED_EVERY_BASE = 4, 256
+
+
+def perm_code(perm) -> int:
+    """A permutation name (RV, NI, ND, RAND) or schedule name (ND-RAND%x,
+    ND-RAND%2^i; Sec. 4.2.1) as the oracle's integer code; ints pass through."""
+    if not isinstance(perm, str):
+        return int(perm)
+    p = perm.upper()
+    if p in PERMS:
+        return PERMS[p]
+    if p == "ND-RAND%2^I":
+        return SCHED_POW2
+    if p.startswith("ND-RAND%"):
+        return SCHED_EVERY_BASE + int(p[len("ND-RAND%"):])
+    raise KeyError(perm)
 
 
 class OracleError(RuntimeError):
@@ -84,6 +101,8 @@ def _load():
         lib.oracle_class_order.restype = ctypes.c_int32
         lib.oracle_recolor.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_uint64, P, P]
+        lib.oracle_perm_of_iteration.argtypes = [ctypes.c_int32, ctypes.c_int32]
+        lib.oracle_perm_of_iteration.restype = ctypes.c_int32
         for f in (lib.oracle_color, lib.oracle_color_tables, lib.oracle_validate,
                   lib.oracle_recolor):
             f.restype = ctypes.c_int
@@ -121,6 +140,12 @@ def rxf_draw(seed: int, v: int, r: int) -> int:
 
 def perm_draw(seed: int, i: int, it: int) -> int:
     return int(_load().oracle_perm_draw(seed, i, it))
+
+
+def perm_of_iteration(perm, it: int) -> int:
+    """The permutation (0..3) recoloring iteration `it` (0-based) uses under a
+    permutation or schedule; -1 for an unknown code."""
+    return int(_load().oracle_perm_of_iteration(perm_code(perm), it))
 
 
 def color(off, idx, X: int = 1, seed: int = 0):
@@ -193,7 +218,7 @@ def recolor(off, idx, colors_in, perm="RV", iterations: int = 1, seed: int = 0):
     cin = np.ascontiguousarray(colors_in, dtype=np.int32)
     out = np.zeros(n, dtype=np.int32)
     nc = np.zeros(iterations + 1, dtype=np.int32)
-    rc = lib.oracle_recolor(n, _ptr(off), _ptr(idx), _ptr(cin), PERMS.get(perm, perm),
+    rc = lib.oracle_recolor(n, _ptr(off), _ptr(idx), _ptr(cin), perm_code(perm),
                             iterations, seed, _ptr(out), _ptr(nc))
     if rc != OK:
         raise OracleError(rc, "recolor")

@@ -42,7 +42,12 @@
  *     present colors, i = k-1 .. 1, j = floor(w0 * (i+1) / 2^32) with
  *     w0 = Philox(seed, (i, it, 0, 3)).w0, it the iteration number;
  *   - within a class, vertices are visited in increasing id (any order gives
- *     the same result, a class being an independent set).
+ *     the same result, a class being an independent set);
+ *   - permutation schedules (Sec. 4.2.1): ND-RAND%x uses RAND at iterations
+ *     x, 2x, 3x, ... and ND at the others; ND-RAND%2^i uses RAND at the
+ *     iterations that are powers of two from 2 on (2, 4, 8, ...) and ND at
+ *     the others; iterations are counted from 1 there, so iteration t uses
+ *     the RAND draws of iteration number t - 1 above.
  *
  * The Philox4x32-10 generator is written from its published definition
  * (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
@@ -67,6 +72,10 @@
 #define PERM_NONINC 1
 #define PERM_NONDEC 2
 #define PERM_RANDOM 3
+/* schedules: 4 = ND-RAND%2^i; 256 + x = ND-RAND%x, 1 <= x <= 65535 */
+#define SCHED_POW2 4
+#define SCHED_EVERY_BASE 256
+#define SCHED_EVERY_MAX (256 + 65535)
 
 #define TAG_PRIO 1u
 #define TAG_RXF 2u
@@ -438,6 +447,24 @@ int32_t oracle_class_order(int32_t maxc, const int64_t* size, int32_t perm,
     return k;
 }
 
+/* The permutation that recoloring iteration `it` (0-based) uses under a
+ * permutation or schedule code (Sec. 4.2.1), or -1 if the code is unknown. */
+int32_t oracle_perm_of_iteration(int32_t code, int32_t it)
+{
+    int32_t t = it + 1;                 /* the paper counts iterations from 1 */
+    if (code >= PERM_REVERSE && code <= PERM_RANDOM) return code;
+    if (code == SCHED_POW2) {
+        int32_t p = 2;
+        while (p < t && p <= (1 << 29)) p *= 2;
+        return p == t ? PERM_RANDOM : PERM_NONDEC;
+    }
+    if (code > SCHED_EVERY_BASE && code <= SCHED_EVERY_MAX) {
+        int32_t x = code - SCHED_EVERY_BASE;
+        return t % x == 0 ? PERM_RANDOM : PERM_NONDEC;
+    }
+    return -1;
+}
+
 /* ------------------------------------------------------------------ */
 /* Iterative recoloring (Culberson's iterated greedy, Sec. 2.1; RC Sec. 3) */
 /* ------------------------------------------------------------------ */
@@ -457,7 +484,7 @@ int oracle_recolor(int64_t n, const int64_t* off, const int32_t* idx,
     int status;
     oracle_validation val;
 
-    if (iterations < 0 || perm < PERM_REVERSE || perm > PERM_RANDOM)
+    if (iterations < 0 || oracle_perm_of_iteration(perm, 0) < 0)
         return OR_ERR_INVALID_ARG;
     status = oracle_validate(n, off, idx, colors_in, &val);
     if (status != OR_OK) return status;
@@ -492,7 +519,7 @@ int oracle_recolor(int64_t n, const int64_t* off, const int32_t* idx,
             members[start[c] + fill[c]] = v;
             fill[c]++;
         }
-        k = oracle_class_order(maxc, size, perm, seed, it, NULL, order);
+        k = oracle_class_order(maxc, size, oracle_perm_of_iteration(perm, it), seed, it, NULL, order);
 
         /* Alg. 1 over the vertices taken class after class in the order
          * chosen; a vertex not recolored yet has new color 0 and so does not

@@ -293,6 +293,60 @@ def test_brute_force_chromatic_lower_bound(seed):
 
 
 # --------------------------------------------------------------------------
+# ND-RAND permutation schedules (Sec. 4.2.1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", _load("nd_rand_schedules.json")["cases"], ids=lambda c: c["schedule"])
+def test_schedule_rand_iterations_match_the_paper(case):
+    perms = [oracle.perm_of_iteration(case["schedule"], t) for t in range(case["iterations"])]
+    assert [t + 1 for t, p in enumerate(perms) if p == oracle.PERM_RANDOM] == case["rand_at"]
+    assert all(p in (oracle.PERM_RANDOM, oracle.PERM_NONDEC) for p in perms)
+
+
+@pytest.mark.parametrize("schedule,iters", [("ND-RAND%3", 7), ("ND-RAND%2^i", 9), ("ND-RAND%1", 3)])
+def test_schedule_recolor_is_the_iterations_composed(schedule, iters):
+    """Each iteration is one RC pass (computed here class by class, outside
+    the oracle) in the order ND, or RAND drawn with that iteration's number."""
+    rand_at = {t for t in range(1, iters + 1)
+               if oracle.perm_of_iteration(schedule, t - 1) == oracle.PERM_RANDOM}
+    for seed in range(3):
+        g = gg.erdos_renyi(300, 10.0, seed=70 + seed)
+        off, idx = _np(g)
+        c, _ = oracle.color(off, idx, 6, seed)
+        cur = c.astype(np.int64)
+        for t in range(1, iters + 1):
+            sizes = np.bincount(cur, minlength=cur.max() + 1)
+            if t in rand_at:
+                order = oracle.class_order(sizes, "RAND", seed=seed + 9, iteration=t - 1)
+            else:
+                order = oracle.class_order(sizes, "ND")
+            cur = _class_parallel_recolor(off, idx, cur, order)
+        out, nc = oracle.recolor(off, idx, c, schedule, iters, seed=seed + 9)
+        assert np.array_equal(out, cur)
+        assert np.all(np.diff(nc) <= 0)
+
+
+def test_schedule_without_a_rand_iteration_is_nd():
+    g = gg.erdos_renyi(500, 14.0, seed=5)
+    off, idx = _np(g)
+    c, _ = oracle.color(off, idx, 3, 2)
+    nd, _ = oracle.recolor(off, idx, c, "ND", 4)
+    assert np.array_equal(oracle.recolor(off, idx, c, "ND-RAND%5", 4, seed=1)[0], nd)
+    assert np.array_equal(oracle.recolor(off, idx, c, "ND-RAND%2^i", 1, seed=1)[0],
+                          oracle.recolor(off, idx, c, "ND", 1)[0])
+
+
+def test_schedule_codes_out_of_range():
+    g = gg.path(3)
+    off, idx = _np(g)
+    c = np.array([1, 2, 1], dtype=np.int32)
+    for bad in (oracle.SCHED_EVERY_BASE, oracle.SCHED_EVERY_BASE + 65536, 5, -1):
+        with pytest.raises(oracle.OracleError):
+            oracle.recolor(off, idx, c, bad, 1)
+        assert oracle.perm_of_iteration(bad, 0) == -1
+
+
+# --------------------------------------------------------------------------
 # Class orders and the generator
 # --------------------------------------------------------------------------
 
