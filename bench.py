@@ -50,6 +50,14 @@ WORKLOADS = {
                    perm_seed=5,
                    label="R-MAT scale 24 ef 16 (0.57,0.19,0.19,0.05) seed 4; First Fit "
                          "+ 20 recoloring iterations RAND (seed 5)"),
+    "st27-128-quality": dict(graph="st27-128", strategy="RXF", X=5, seed=3, perm="ND", iterations=1,
+                             perm_seed=0,
+                             label="27-point stencil 128^3, ids shuffled (seed 2); the 'quality' "
+                                   "preset: Random-5 Fit (seed 3) + 1 ND iteration"),
+    "rmat24-ndrand": dict(graph="rmat24", strategy="FF", X=1, seed=7, perm="ND-RAND%2^i", iterations=20,
+                          perm_seed=5,
+                          label="R-MAT scale 24 ef 16 (0.57,0.19,0.19,0.05) seed 4; First Fit + 20 "
+                                "recoloring iterations ND-RAND%2^i (seed 5)"),
     "batch": dict(label="batch"),
     "serve": dict(label="serve"),
     "er10k": dict(graph="er10k", strategy="FF", X=1, seed=1, perm="RV", iterations=2, perm_seed=0,

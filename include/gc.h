@@ -83,8 +83,23 @@ typedef enum {
     GC_PERM_REVERSE = 0, /* RV: decreasing color                              */
     GC_PERM_NONINC = 1,  /* NI: non-increasing class size, ties smaller color */
     GC_PERM_NONDEC = 2,  /* ND: non-decreasing class size, ties smaller color */
-    GC_PERM_RANDOM = 3   /* RAND: seeded Knuth shuffle                        */
+    GC_PERM_RANDOM = 3,  /* RAND: seeded Knuth shuffle                        */
+    /* Schedules (Sec. 4.2.1), iterations counted from 1: ND at every iteration
+     * except 2, 4, 8, 16, ..., which use RAND (ND-RAND%2^i) */
+    GC_PERM_ND_RAND_POW2 = 4
 } gc_perm;
+/* ND-RAND%x (Sec. 4.2.1): RAND at iterations x, 2x, 3x, ..., ND at the
+ * others; 1 <= x <= 65535.  Accepted wherever a gc_perm is.  An iteration
+ * that uses RAND draws its shuffle with its own iteration number, as plain
+ * RAND does. */
+#define GC_PERM_ND_RAND_EVERY(x) (256 + (x))
+
+/* Parameter sets of Sec. 4.3 and Sec. 5: "speed" is First Fit with no
+ * recoloring (FIxxND0); "quality" is Random-5 Fit (or Random-10 Fit) with
+ * one ND recoloring iteration (R(5|10)IxxND1).  The internal-first vertex
+ * order of those names is a distributed-memory notion with no counterpart on
+ * one GPU, where every vertex is its own processor. */
+typedef enum { GC_PRESET_SPEED = 0, GC_PRESET_QUALITY = 1, GC_PRESET_QUALITY_X10 = 2 } gc_preset;
 
 typedef enum { GC_MEM_DEVICE = 0, GC_MEM_HOST = 1 } gc_memspace;
 
@@ -385,6 +400,11 @@ void gc_profile_enable(int32_t on);
 int32_t gc_profile_read(gc_kernel_time* out, int32_t max);
 
 /* Static description of a status code. */
+/* The strategy, X, permutation and iteration count of a preset (host only;
+ * any pointer may be NULL).  GC_ERR_INVALID_ARG for an unknown preset. */
+gc_status gc_preset_params(gc_preset preset, int32_t* strategy, int32_t* X, int32_t* perm,
+                           int32_t* iterations);
+
 const char* gc_status_string(gc_status s);
 
 /* Library version, major * 10000 + minor * 100 + patch. */

@@ -25,7 +25,7 @@ __all__ = [
     "gc_check_graph", "gc_server_create", "gc_server_submit", "gc_server_poll", "gc_server_wait",
     "gc_server_stats", "gc_server_destroy",
     "gc_priorities", "gc_set_tuning", "gc_get_tuning", "gc_profile_enable", "gc_profile_read",
-    "gc_kernel_launches", "gc_status_string", "gc_version",
+    "gc_kernel_launches", "gc_status_string", "gc_version", "gc_preset_params",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -147,6 +147,8 @@ def load():
         lib.gc_server_wait.argtypes = [H, ctypes.c_uint64, P, ctypes.POINTER(_RequestResult),
                                        ctypes.c_int32]
         lib.gc_server_stats.argtypes = [H, ctypes.POINTER(_ServerInfo)]
+        lib.gc_preset_params.argtypes = [ctypes.c_int, P, P, P, P]
+        lib.gc_preset_params.restype = ctypes.c_int
         lib.gc_server_destroy.argtypes = [H]
         lib.gc_server_destroy.restype = None
         for f in ("gc_color", "gc_recolor", "gc_color_recolor", "gc_validate", "gc_validate_noalloc",
@@ -208,8 +210,26 @@ def _strategy(s):
     return int(s)
 
 
+PERM_ND_RAND_POW2 = 4
+
+
+def PERM_ND_RAND_EVERY(x: int) -> int:
+    """gc_perm code of the ND-RAND%x schedule (Sec. 4.2.1)."""
+    return 256 + int(x)
+
+
 def _perm(p):
-    return PERM[p.upper()] if isinstance(p, str) else int(p)
+    """A gc_perm code from RV/NI/ND/RAND, ND-RAND%x or ND-RAND%2^i (ints pass through)."""
+    if not isinstance(p, str):
+        return int(p)
+    u = p.upper()
+    if u in PERM:
+        return PERM[u]
+    if u == "ND-RAND%2^I":
+        return PERM_ND_RAND_POW2
+    if u.startswith("ND-RAND%"):
+        return PERM_ND_RAND_EVERY(int(u[len("ND-RAND%"):]))
+    raise KeyError(p)
 
 
 def _check_colors(t: torch.Tensor, n: int, device, name: str):
@@ -516,6 +536,21 @@ def gc_profile_read():
     arr = (_KernelTime * max(cnt, 1))()
     cnt = lib.gc_profile_read(arr, cnt)
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms)) for i in range(cnt)}
+
+
+PRESETS = {"speed": 0, "quality": 1, "quality10": 2}
+
+
+def gc_preset_params(preset):
+    """The parameter sets of Sec. 4.3 / Sec. 5 ("speed", "quality", "quality10")
+    as keyword arguments of gc_color_recolor."""
+    lib = load()
+    s, x, p, it = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    code = PRESETS[preset] if isinstance(preset, str) else int(preset)
+    _check(lib.gc_preset_params(code, ctypes.byref(s), ctypes.byref(x), ctypes.byref(p), ctypes.byref(it)),
+           "gc_preset_params")
+    return {"strategy": "FF" if s.value == FIRST_FIT else "RXF", "X": x.value,
+            "perm": {v: k for k, v in PERM.items()}.get(p.value, p.value), "iterations": it.value}
 
 
 def gc_kernel_launches() -> int:

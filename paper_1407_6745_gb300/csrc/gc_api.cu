@@ -296,7 +296,7 @@ static gc_status gc_recolor_impl(const gc_graph* g, const int32_t* colors_in, gc
                      void* stream) {
     gc_status st = check_graph_args(g);
     if (st != GC_OK) return st;
-    if (perm < GC_PERM_REVERSE || perm > GC_PERM_RANDOM || iterations < 0) return GC_ERR_INVALID_ARG;
+    if (!perm_valid(perm) || iterations < 0) return GC_ERR_INVALID_ARG;
     if (g->n > 0 && (!colors_in || !colors_out)) return GC_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     DeviceGraph dg;
@@ -322,7 +322,7 @@ static gc_status gc_color_recolor_impl(const gc_graph* g, gc_strategy strategy, 
     if (st != GC_OK) return st;
     if (strategy != GC_FIRST_FIT && strategy != GC_RANDOM_X_FIT) return GC_ERR_INVALID_ARG;
     if (strategy == GC_FIRST_FIT) X = 1;
-    if (X < 1 || perm < GC_PERM_REVERSE || perm > GC_PERM_RANDOM || iterations < 0)
+    if (X < 1 || !perm_valid(perm) || iterations < 0)
         return GC_ERR_INVALID_ARG;
     if (g->n > 0 && !colors_out) return GC_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -627,6 +627,22 @@ gc_status gc_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64
     if (st != GC_OK) return st;
     *best = cur;
     if (best_ms) *best_ms = cur_ms;
+    return GC_OK;
+}
+
+gc_status gc_preset_params(gc_preset preset, int32_t* strategy, int32_t* X, int32_t* perm,
+                           int32_t* iterations) {
+    int32_t s_, x_, p_, i_;
+    switch (preset) {
+    case GC_PRESET_SPEED: s_ = GC_FIRST_FIT; x_ = 1; p_ = GC_PERM_NONDEC; i_ = 0; break;
+    case GC_PRESET_QUALITY: s_ = GC_RANDOM_X_FIT; x_ = 5; p_ = GC_PERM_NONDEC; i_ = 1; break;
+    case GC_PRESET_QUALITY_X10: s_ = GC_RANDOM_X_FIT; x_ = 10; p_ = GC_PERM_NONDEC; i_ = 1; break;
+    default: return GC_ERR_INVALID_ARG;
+    }
+    if (strategy) *strategy = s_;
+    if (X) *X = x_;
+    if (perm) *perm = p_;
+    if (iterations) *iterations = i_;
     return GC_OK;
 }
 

@@ -796,7 +796,7 @@ gc_status batch_layout(const Graph& g, const gc_batch_graph* graphs, int32_t ng,
     int32_t mx = 1;
     for (int32_t i = 0; i < ng; ++i) {
         const gc_batch_graph& d = graphs[i];
-        if (d.vertex_base != next || d.n < 0 || d.X < 1 || d.iterations < 0 || d.perm < 0 || d.perm > 3)
+        if (d.vertex_base != next || d.n < 0 || d.X < 1 || d.iterations < 0 || !perm_valid(d.perm))
             return GC_ERR_INVALID_ARG;
         next += d.n;
         mx = std::max(mx, d.X);

@@ -58,6 +58,19 @@ __host__ __device__ inline int bucket_of(int64_t deg, int32_t X, const Tuning& t
     return deg <= t.warp_max_deg ? 1 : 0;
 }
 
+// The permutation (RV/NI/ND/RAND = 0..3) of recoloring iteration `it`
+// (0-based) under a gc_perm code, schedules included (Sec. 4.2.1: the paper
+// counts iterations from 1); -1 for an unknown code.
+constexpr int32_t kSchedPow2 = 4, kSchedEveryBase = 256, kSchedEveryMax = 256 + 65535;
+__host__ __device__ inline int32_t perm_at(int32_t code, int32_t it) {
+    if (code >= 0 && code <= 3) return code;
+    const int32_t t = it + 1;
+    if (code == kSchedPow2) return (t >= 2 && (t & (t - 1)) == 0) ? 3 : 2;
+    if (code > kSchedEveryBase && code <= kSchedEveryMax) return t % (code - kSchedEveryBase) == 0 ? 3 : 2;
+    return -1;
+}
+__host__ __device__ inline bool perm_valid(int32_t code) { return perm_at(code, 0) >= 0; }
+
 // One graph of a batch (same layout as gc_batch_graph).
 struct BatchDesc {
     int64_t base;

@@ -286,11 +286,12 @@ __global__ void __launch_bounds__(kOrderThreads) k_rc_order(RcArgs a) {
     __syncthreads();
     if (a.iteration == 0 && t == 0) a.ncolors[0] = k > 0 ? a.present[k - 1] : 0;
 
-    // the permutation (Sec. 3)
-    if (a.perm == 0) {  // RV
+    // the permutation (Sec. 3) of this iteration (Sec. 4.2.1 schedules)
+    const int32_t perm = perm_at(a.perm, a.iteration);
+    if (perm == 0) {  // RV
         for (int32_t i = t; i < k; i += kOrderThreads) a.order[i] = a.present[k - 1 - i];
-    } else if (a.perm == 1 || a.perm == 2) {  // NI / ND, ties to the smaller color
-        const bool noninc = a.perm == 1;
+    } else if (perm == 1 || perm == 2) {  // NI / ND, ties to the smaller color
+        const bool noninc = perm == 1;
         for (int32_t i = t; i < k; i += kOrderThreads) {
             const int32_t si = a.psize[i];
             int32_t r = 0;
@@ -742,10 +743,11 @@ __global__ void __launch_bounds__(kBlock) k_brc_order(RcArgs a) {
             k += __popc(bal);
         }
         __syncwarp();
-        if (d.perm == 0) {
+        const int32_t perm = perm_at(d.perm, a.iteration);
+        if (perm == 0) {
             for (int32_t i = l; i < k; i += 32) order[i] = present[k - 1 - i];
-        } else if (d.perm == 1 || d.perm == 2) {
-            const bool noninc = d.perm == 1;
+        } else if (perm == 1 || perm == 2) {
+            const bool noninc = perm == 1;
             for (int32_t i = l; i < k; i += 32) {
                 const int32_t si = psize[i];
                 int32_t r = 0;

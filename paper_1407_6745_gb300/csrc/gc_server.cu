@@ -350,7 +350,7 @@ gc_status gc_server_submit(gc_server* s, const gc_request* q, uint64_t* ticket) 
         (g.mem != GC_MEM_DEVICE && g.mem != GC_MEM_HOST) || !g.offsets || (g.nnz > 0 && !g.idx))
         return GC_ERR_INVALID_ARG;
     if ((q->strategy != GC_FIRST_FIT && q->strategy != GC_RANDOM_X_FIT) ||
-        (q->strategy == GC_RANDOM_X_FIT && q->X < 1) || q->iterations < 0 || q->perm < 0 || q->perm > 3)
+        (q->strategy == GC_RANDOM_X_FIT && q->X < 1) || q->iterations < 0 || !perm_valid(q->perm))
         return GC_ERR_INVALID_ARG;
     Request* r = new Request();
     r->n = g.n;

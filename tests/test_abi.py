@@ -72,3 +72,25 @@ def test_server_struct_layouts():
     assert ctypes.sizeof(gc._Request) == 40 + 4 + 4 + 8 + 4 + 4 + 8
     assert ctypes.sizeof(gc._RequestResult) == 4 * 4 + 3 * 8
     assert ctypes.sizeof(gc._ServerInfo) == 4 * 8 + 4 * 8 + 2 * 8
+
+
+def test_presets_are_the_papers_parameter_sets():
+    """gc_preset_params returns the parameter sets named in Sec. 4.3 / Sec. 5
+    (tests/golden/nd_rand_schedules.json)."""
+    import json
+    import paper_1407_6745_gb300 as gc
+    with open(os.path.join(ROOT, "tests", "golden", "nd_rand_schedules.json")) as f:
+        presets = json.load(f)["presets"]
+    for name in ("speed", "quality", "quality10"):
+        want = presets[name]
+        assert gc.gc_preset_params(name) == want
+    with pytest.raises(gc.GCError):
+        gc.gc_preset_params(7)
+
+
+def test_schedule_codes_match_the_oracle():
+    """The binding's schedule names map to the codes the oracle uses."""
+    import oracle
+    import paper_1407_6745_gb300 as gc
+    for name in ("RV", "NI", "ND", "RAND", "ND-RAND%5", "ND-RAND%10", "ND-RAND%2^i", "ND-RAND%1"):
+        assert gc._perm(name) == oracle.perm_code(name)

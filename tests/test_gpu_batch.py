@@ -1,6 +1,7 @@
 """Batched coloring and recoloring: each graph of a batch gets exactly the
 colors it gets alone (and from the oracle), whatever the mix of sizes,
-strategies, permutations and iteration counts in the batch."""
+strategies, permutations (schedules included) and iteration counts in the
+batch."""
 import numpy as np
 import pytest
 import torch
@@ -29,7 +30,8 @@ def _mixed_batch(count, seed):
     desc = []
     for i, g in enumerate(graphs):
         desc.append(dict(n=g.n, seed=int(rng.integers(1 << 40)), X=int(rng.choice([1, 1, 3, 8])),
-                         perm=["RV", "NI", "ND", "RAND"][i % 4], iterations=int(rng.integers(0, 6)),
+                         perm=["RV", "NI", "ND", "RAND", "ND-RAND%2", "ND-RAND%2^i"][i % 6],
+                         iterations=int(rng.integers(0, 6)),
                          perm_seed=int(rng.integers(1 << 40))))
     return graphs, desc
 

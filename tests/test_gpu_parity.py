@@ -103,6 +103,27 @@ def test_every_permutation(perm):
     _recolor(g, c, perm, 4, 13)
 
 
+@pytest.mark.parametrize("schedule,iters", [("ND-RAND%3", 7), ("ND-RAND%2^i", 9), ("ND-RAND%1", 3),
+                                             ("ND-RAND%10", 12)])
+def test_nd_rand_schedules(schedule, iters):
+    """Sec. 4.2.1 schedules: ND at most iterations, RAND at the scheduled ones."""
+    for g in (gg.erdos_renyi(6000, 20.0, seed=12), gg.workload("rmat12"), gg.workload("st27-16")):
+        c = _spec(g, "RXF", 6, 4)
+        _recolor(g, c, schedule, iters, 21)
+
+
+@pytest.mark.parametrize("preset", ["speed", "quality", "quality10"])
+def test_presets(preset):
+    """The "speed" and "quality" parameter sets of Sec. 4.3, end to end."""
+    p = gc.gc_preset_params(preset)
+    g = gg.workload("st27-24")
+    off, idx = g.numpy()
+    oc, _ = oracle.color(off, idx, p["X"], 17)
+    orc, onc = oracle.recolor(off, idx, oc, p["perm"], p["iterations"], 0)
+    nc = _pipeline(g, p["strategy"], p["X"], 17, p["perm"], p["iterations"], 0, orc)
+    assert nc == onc.tolist()
+
+
 # --------------------------------------------------------------------------
 # Scheduling thresholds and bitmap windows
 # --------------------------------------------------------------------------

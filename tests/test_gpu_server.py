@@ -48,7 +48,8 @@ def _mix(seed):
     for i, g in enumerate(graphs * 2):
         strategy = "FF" if rng.random() < 0.5 else "RXF"
         reqs.append(dict(graph=g, strategy=strategy, X=1 if strategy == "FF" else int(rng.integers(2, 40)),
-                         seed=int(rng.integers(0, 2**63)), perm=["RV", "NI", "ND", "RAND"][i % 4],
+                         seed=int(rng.integers(0, 2**63)),
+                         perm=["RV", "NI", "ND", "RAND", "ND-RAND%3", "ND-RAND%2^i"][i % 6],
                          iterations=int(rng.integers(0, 21)), perm_seed=int(rng.integers(0, 2**32))))
     return reqs
 
