@@ -10,7 +10,8 @@ with gcc into ``liboracle.so`` next to it); this module only marshals numpy
 arrays.  Passages followed: Alg. 1 and First Fit (Sec. 2.1), the speculative
 rounds of Sec. 2.2, Random-X Fit (Sec. 3.2), recoloring and the class
 permutations RV/NI/ND/RAND (Sec. 2.1, Sec. 3) and their ND-RAND schedules
-(Sec. 4.2.1).  The readings taken where the
+(Sec. 4.2.1), Largest-First priorities (Sec. 2.2.1) and asynchronous
+recoloring (aRC, Sec. 3).  The readings taken where the
 paper is silent are listed at the top of ``gc_oracle.c``.
 """
 from __future__ import annotations
@@ -101,6 +102,14 @@ def _load():
         lib.oracle_class_order.restype = ctypes.c_int32
         lib.oracle_recolor.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_uint64, P, P]
+        lib.oracle_color_lf.argtypes = [ctypes.c_int64, P, P, ctypes.c_int32, ctypes.c_uint64,
+                                        P, ctypes.POINTER(ColorStats)]
+        lib.oracle_color_lf.restype = ctypes.c_int
+        lib.oracle_recolor_async.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_uint64, P, P, P]
+        lib.oracle_recolor_async.restype = ctypes.c_int
+        lib.oracle_ordered_priority.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64]
+        lib.oracle_ordered_priority.restype = ctypes.c_uint32
         lib.oracle_perm_of_iteration.argtypes = [ctypes.c_int32, ctypes.c_int32]
         lib.oracle_perm_of_iteration.restype = ctypes.c_int32
         for f in (lib.oracle_color, lib.oracle_color_tables, lib.oracle_validate,
@@ -209,6 +218,41 @@ def class_order(sizes, perm, seed: int = 0, iteration: int = 0, draws=None):
     if k < 0:
         raise OracleError(k, "class_order")
     return order[:k].copy()
+
+
+def ordered_priority(first_key: int, seed: int, v: int) -> int:
+    """Conflict priority with a vertex-visit key first (LF degree, aRC rank)."""
+    return int(_load().oracle_ordered_priority(first_key, seed, v))
+
+
+def color_lf(off, idx, X: int = 1, seed: int = 0):
+    """Speculative coloring where the larger degree wins a conflict (Largest
+    First, Sec. 2.2.1).  Returns (colors, stats) as color()."""
+    lib = _load()
+    off, idx, n = _graph(off, idx)
+    out = np.zeros(n, dtype=np.int32)
+    st = ColorStats()
+    rc = lib.oracle_color_lf(n, _ptr(off), _ptr(idx), X, seed, _ptr(out), ctypes.byref(st))
+    if rc != OK:
+        raise OracleError(rc, "color_lf")
+    return out, {"rounds": st.rounds, "max_color": st.max_color,
+                 "edges_examined": st.edges_examined, "conflicts": st.conflicts}
+
+
+def recolor_async(off, idx, colors_in, perm="RV", iterations: int = 1, seed: int = 0):
+    """Asynchronous recoloring (aRC, Sec. 3).  Returns (colors,
+    ncolors int32[iterations+1], rounds int32[iterations])."""
+    lib = _load()
+    off, idx, n = _graph(off, idx)
+    cin = np.ascontiguousarray(colors_in, dtype=np.int32)
+    out = np.zeros(n, dtype=np.int32)
+    nc = np.zeros(iterations + 1, dtype=np.int32)
+    rounds = np.zeros(max(iterations, 1), dtype=np.int32)
+    rc = lib.oracle_recolor_async(n, _ptr(off), _ptr(idx), _ptr(cin), perm_code(perm), iterations,
+                                  seed, _ptr(out), _ptr(nc), _ptr(rounds))
+    if rc != OK:
+        raise OracleError(rc, "recolor_async")
+    return out, nc, rounds[:iterations]
 
 
 def recolor(off, idx, colors_in, perm="RV", iterations: int = 1, seed: int = 0):

@@ -43,6 +43,13 @@
  *     w0 = Philox(seed, (i, it, 0, 3)).w0, it the iteration number;
  *   - within a class, vertices are visited in increasing id (any order gives
  *     the same result, a class being an independent set);
+ *   - vertex-visit orderings become the first key of the conflict priority
+ *     (one GPU thread per vertex leaves no visit order): Largest First
+ *     (Sec. 2.2.1) uses min(deg(v), 65535); asynchronous recoloring (aRC,
+ *     Sec. 3) colors again from scratch by the speculative rounds with First
+ *     Fit, the first key being 65535 - min(rank, 65535), rank the position
+ *     of v's previous color class in the iteration's class permutation; the
+ *     second key is the upper 16 bits of the Philox priority, then the id;
  *   - permutation schedules (Sec. 4.2.1): ND-RAND%x uses RAND at iterations
  *     x, 2x, 3x, ... and ND at the others; ND-RAND%2^i uses RAND at the
  *     iterations that are powers of two from 2 on (2, 4, 8, ...) and ND at
@@ -554,5 +561,116 @@ int oracle_recolor(int64_t n, const int64_t* off, const int32_t* idx,
 done:
     free(old); free(nw); free(members); free(forbidden);
     free(size); free(start); free(fill); free(order);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Vertex-visit orders as conflict priorities: Largest First            */
+/* (Sec. 2.2.1) and asynchronous recoloring (aRC, Sec. 3)              */
+/* ------------------------------------------------------------------ */
+
+/* A visit-order key (clamped to 16 bits) above the upper half of the
+ * Philox priority; equal pairs fall back to the id, as in every round. */
+static uint32_t ordered_priority(uint32_t first_key, uint64_t seed, int64_t v)
+{
+    if (first_key > 65535u) first_key = 65535u;
+    return (first_key << 16) | (oracle_priority(seed, v) >> 16);
+}
+
+uint32_t oracle_ordered_priority(uint32_t first_key, uint64_t seed, int64_t v)
+{
+    return ordered_priority(first_key, seed, v);
+}
+
+/* Speculative coloring in which a larger degree wins a conflict. */
+int oracle_color_lf(int64_t n, const int64_t* off, const int32_t* idx, int32_t X,
+                    uint64_t seed, int32_t* colors_out, oracle_color_stats* st)
+{
+    rng_source src;
+    uint32_t* prio;
+    int64_t v;
+    int status;
+    if (n > 0 && !colors_out) return OR_ERR_INVALID_ARG;
+    status = check_graph(n, off, idx);
+    if (status != OR_OK) return status;
+    prio = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    if (!prio) return OR_ERR_OOM;
+    for (v = 0; v < n; ++v) {
+        int64_t d = off[v + 1] - off[v];
+        prio[v] = ordered_priority((uint32_t)(d > 65535 ? 65535 : d), seed, v);
+    }
+    src.seed = seed; src.prio_tab = prio; src.draw_tab = NULL;
+    src.draw_rounds = 0; src.n = n;
+    status = color_core(n, off, idx, X, &src, colors_out, st);
+    free(prio);
+    return status;
+}
+
+/* aRC: each iteration colors the graph again by speculative First-Fit
+ * rounds, a vertex of an earlier class (in the iteration's permutation of
+ * the previous coloring's classes) winning its conflicts.  ncolors as for
+ * oracle_recolor; rounds (may be NULL) receives each iteration's rounds. */
+int oracle_recolor_async(int64_t n, const int64_t* off, const int32_t* idx,
+                         const int32_t* colors_in, int32_t perm, int32_t iterations,
+                         uint64_t seed, int32_t* colors_out, int32_t* ncolors,
+                         int32_t* rounds)
+{
+    int32_t *old = NULL, *nw = NULL, *order = NULL, *rank = NULL;
+    int64_t *size = NULL;
+    uint32_t* prio = NULL;
+    int64_t v;
+    int32_t it, maxc, c, k, p;
+    int status;
+    oracle_validation val;
+    oracle_color_stats st;
+    rng_source src;
+
+    if (iterations < 0 || oracle_perm_of_iteration(perm, 0) < 0) return OR_ERR_INVALID_ARG;
+    status = oracle_validate(n, off, idx, colors_in, &val);
+    if (status != OR_OK) return status;
+    if (val.n_conflicts > 0 || val.n_uncolored > 0) return OR_ERR_IMPROPER_INPUT;
+    if (ncolors) ncolors[0] = val.max_color;
+    if (n == 0) {
+        for (it = 0; it < iterations; ++it) {
+            if (ncolors) ncolors[it + 1] = 0;
+            if (rounds) rounds[it] = 0;
+        }
+        return OR_OK;
+    }
+    old = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    nw = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    prio = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n);
+    if (!old || !nw || !prio) { status = OR_ERR_OOM; goto done; }
+    memcpy(old, colors_in, sizeof(int32_t) * (size_t)n);
+    maxc = val.max_color;
+    for (it = 0; it < iterations; ++it) {
+        size = (int64_t*)calloc((size_t)maxc + 1, sizeof(int64_t));
+        order = (int32_t*)malloc(sizeof(int32_t) * ((size_t)maxc + 1));
+        rank = (int32_t*)malloc(sizeof(int32_t) * ((size_t)maxc + 1));
+        if (!size || !order || !rank) { status = OR_ERR_OOM; goto done; }
+        for (v = 0; v < n; ++v) size[old[v]]++;
+        k = oracle_class_order(maxc, size, oracle_perm_of_iteration(perm, it), seed, it, NULL, order);
+        for (c = 0; c <= maxc; ++c) rank[c] = 0;
+        for (p = 0; p < k; ++p) rank[order[p]] = p;
+        for (v = 0; v < n; ++v) {
+            int32_t r = rank[old[v]];
+            prio[v] = ordered_priority(65535u - (uint32_t)(r > 65535 ? 65535 : r), seed, v);
+        }
+        src.seed = seed; src.prio_tab = prio; src.draw_tab = NULL;
+        src.draw_rounds = 0; src.n = n;
+        status = color_core(n, off, idx, 1, &src, nw, &st);
+        if (status != OR_OK) goto done;
+        memcpy(old, nw, sizeof(int32_t) * (size_t)n);
+        maxc = st.max_color;
+        if (ncolors) ncolors[it + 1] = maxc;
+        if (rounds) rounds[it] = st.rounds;
+        free(size); free(order); free(rank);
+        size = NULL; order = NULL; rank = NULL;
+    }
+    memcpy(colors_out, old, sizeof(int32_t) * (size_t)n);
+    status = OR_OK;
+
+done:
+    free(old); free(nw); free(prio); free(size); free(order); free(rank);
     return status;
 }

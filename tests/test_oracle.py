@@ -347,6 +347,124 @@ def test_schedule_codes_out_of_range():
 
 
 # --------------------------------------------------------------------------
+# Largest First (Sec. 2.2.1) and asynchronous recoloring (aRC, Sec. 3)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("leaves", [2, 5, 40])
+def test_lf_star_hub_keeps_first_color(leaves):
+    """The hub has the largest degree, so it wins round 0 with color 1 and
+    every leaf takes 2 in round 1 (a random order usually loses the hub)."""
+    g = gg.star(leaves)
+    off, idx = _np(g)
+    c, st = oracle.color_lf(off, idx, 1, 3)
+    hub = int(np.argmax(_deg(off)))
+    assert c[hub] == 1 and np.all(np.delete(c, hub) == 2) and st["rounds"] == 2
+
+
+@pytest.mark.parametrize("p,q", [(2, 5), (3, 7), (1, 4)])
+def test_lf_complete_bipartite_closed_form(p, q):
+    """K_{p,q}, p < q: the p side (degree q) beats the q side (degree p)."""
+    g = gg.complete_bipartite(p, q)
+    off, idx = _np(g)
+    c, _ = oracle.color_lf(off, idx, 1, 0)
+    deg = _deg(off)
+    assert np.all(c[deg == q] == 1) and np.all(c[deg == p] == 2)
+
+
+def test_lf_priority_definition_and_path_ends():
+    g = gg.path(5)
+    off, idx = _np(g)
+    for v in range(5):
+        d = int(_deg(off)[v])
+        assert oracle.ordered_priority(d, 9, v) == (d << 16) | (oracle.priority(9, v) >> 16)
+    assert oracle.ordered_priority(70000, 9, 1) >> 16 == 65535
+    # interior vertices (degree 2) beat the ends: round 0 keeps 1 on a maximal
+    # independent subset of the interior
+    c, _ = oracle.color_lf(off, idx, 1, 9)
+    assert oracle.validate(off, idx, c)["n_conflicts"] == 0 and c.max() <= 3
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_lf_bounds_and_regular_graphs(seed):
+    g = gg.erdos_renyi(800, 10.0, seed=seed)
+    off, idx = _np(g)
+    for X in (1, 4):
+        c, st = oracle.color_lf(off, idx, X, seed)
+        assert oracle.validate(off, idx, c)["n_conflicts"] == 0
+        assert np.all(c <= _deg(off) + X)
+    # on a regular graph every degree is equal: LF is the random order with
+    # a 16-bit priority (the same winners as whenever no two upper halves tie)
+    cyc = gg.cycle(101)
+    off, idx = _np(cyc)
+    c, _ = oracle.color_lf(off, idx, 1, seed)
+    assert c.max() == 3
+
+
+@pytest.mark.parametrize("perm", ["RV", "NI", "ND", "RAND"])
+def test_arc_on_complete_graph_equals_rc(perm):
+    """K_n: only the vertex of the earliest class can win each round, so the
+    class of rank r takes color r + 1, exactly as in RC."""
+    g = gg.complete(9)
+    off, idx = _np(g)
+    rng = np.random.default_rng(3)
+    start = (rng.permutation(9) + 1).astype(np.int32)
+    out, nc, rounds = oracle.recolor_async(off, idx, start, perm, 2, seed=4)
+    rc, rnc = oracle.recolor(off, idx, start, perm, 2, seed=4)
+    assert np.array_equal(out, rc) and list(nc) == list(rnc) and list(rounds) == [9, 9]
+
+
+@pytest.mark.parametrize("name", ["grid", "cycle", "kpq"])
+def test_arc_bipartite_two_coloring(name):
+    """A connected bipartite graph with a proper 2-coloring: the earlier class
+    wins round 0 with color 1, the other class takes 2 in round 1."""
+    g = {"grid": gg.grid_2d(9, 7), "cycle": gg.cycle(40), "kpq": gg.complete_bipartite(3, 6)}[name]
+    off, idx = _np(g)
+    # 2-coloring by BFS parity
+    n = len(off) - 1
+    side = np.full(n, -1)
+    side[0] = 0
+    todo = [0]
+    while todo:
+        v = todo.pop()
+        for u in _adj(off, idx, v):
+            if side[u] < 0:
+                side[u] = 1 - side[v]
+                todo.append(u)
+    start = (side + 1).astype(np.int32)
+    for perm in ("RV", "NI", "RAND"):
+        out, nc, rounds = oracle.recolor_async(off, idx, start, perm, 1, seed=1)
+        sizes = np.bincount(start, minlength=3)
+        order = oracle.class_order(sizes, perm, seed=1, iteration=0)
+        assert np.all(out[start == order[0]] == 1) and np.all(out[start == order[1]] == 2)
+        assert rounds[0] == 2
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_arc_properness_bounds_and_rounds(seed):
+    g = gg.erdos_renyi(700, 12.0, seed=30 + seed)
+    off, idx = _np(g)
+    c, _ = oracle.color(off, idx, 5, seed)
+    out, nc, rounds = oracle.recolor_async(off, idx, c, "ND-RAND%2", 5, seed=seed)
+    assert oracle.validate(off, idx, out)["n_conflicts"] == 0
+    assert np.all(out <= _deg(off) + 1)
+    assert nc[-1] == out.max()
+    # a class of rank r is fixed by round r, so an iteration takes at most
+    # as many rounds as the previous coloring has classes
+    cur = c
+    for it in range(5):
+        nxt, _, r = oracle.recolor_async(off, idx, cur, oracle.perm_of_iteration("ND-RAND%2", it), 1, seed=seed)
+        assert r[0] <= len(np.unique(cur))
+        cur = nxt
+    # an edgeless graph keeps one class
+    e = gg.empty(6)
+    eo, ei = _np(e)
+    out, nc, rounds = oracle.recolor_async(eo, ei, np.ones(6, dtype=np.int32), "ND", 2)
+    assert np.all(out == 1) and list(rounds) == [1, 1]
+    with pytest.raises(oracle.OracleError):
+        oracle.recolor_async(off, idx, np.ones(len(off) - 1, dtype=np.int32), "RV", 1)
+
+
+# --------------------------------------------------------------------------
 # Class orders and the generator
 # --------------------------------------------------------------------------
 
