@@ -157,6 +157,34 @@ gc_status gc_recolor(const gc_graph* g, const int32_t* colors_in, gc_perm perm,
                      int32_t* ncolors_per_iter, gc_stats* stats, void* stream);
 
 /*
+ * Speculative coloring with a vertex-visit order as the conflict priority
+ * (Sec. 2.2.1).  GC_ORDER_RANDOM is gc_color.  GC_ORDER_LARGEST_FIRST: of two
+ * neighbors with the same tentative color the one of larger degree keeps
+ * it; the priority is (min(deg, 65535) << 16) | (random priority >> 16),
+ * ties to the larger id.  One thread per vertex leaves no visit order, so
+ * the order acts where a distributed processor's local order would: on
+ * conflicts.  Arguments, memory and errors as gc_color.
+ */
+typedef enum { GC_ORDER_RANDOM = 0, GC_ORDER_LARGEST_FIRST = 1 } gc_order;
+gc_status gc_color_ordered(const gc_graph* g, gc_strategy strategy, int32_t X, uint64_t seed,
+                           gc_order order, int32_t* colors_out, gc_stats* stats, void* stream);
+
+/*
+ * Asynchronous recoloring, aRC (Sec. 3): each iteration colors the graph
+ * again from scratch by the speculative First-Fit rounds, with the class
+ * permutation of the previous coloring (perm, schedules included, RAND keyed
+ * by seed and the iteration number) as the first key of the conflict
+ * priority: (65535 - min(rank, 65535)) << 16 | (random priority >> 16), so a
+ * vertex of an earlier class wins; conflicts make it take rounds, and unlike
+ * gc_recolor the color count may grow.  colors_in must be proper
+ * (GC_ERR_IMPROPER_INPUT); colors_out may alias it; ncolors_per_iter as for
+ * gc_recolor; stats->rounds sums the rounds of all iterations.
+ */
+gc_status gc_recolor_async(const gc_graph* g, const int32_t* colors_in, gc_perm perm,
+                           int32_t iterations, uint64_t seed, int32_t* colors_out,
+                           int32_t* ncolors_per_iter, gc_stats* stats, void* stream);
+
+/*
  * The paper's full method in one call: gc_color followed by `iterations`
  * recoloring iterations of gc_recolor on its (proper by construction)
  * output, with no input re-validation and no intermediate host round trip.

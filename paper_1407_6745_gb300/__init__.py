@@ -26,6 +26,7 @@ __all__ = [
     "gc_server_stats", "gc_server_destroy",
     "gc_priorities", "gc_set_tuning", "gc_get_tuning", "gc_profile_enable", "gc_profile_read",
     "gc_kernel_launches", "gc_status_string", "gc_version", "gc_preset_params",
+    "gc_color_ordered", "gc_recolor_async",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -147,6 +148,11 @@ def load():
         lib.gc_server_wait.argtypes = [H, ctypes.c_uint64, P, ctypes.POINTER(_RequestResult),
                                        ctypes.c_int32]
         lib.gc_server_stats.argtypes = [H, ctypes.POINTER(_ServerInfo)]
+        lib.gc_color_ordered.argtypes = [G, ctypes.c_int, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int,
+                                         P, S, P]
+        lib.gc_recolor_async.argtypes = [G, P, ctypes.c_int, ctypes.c_int32, ctypes.c_uint64, P, P, S, P]
+        for f in ("gc_color_ordered", "gc_recolor_async"):
+            getattr(lib, f).restype = ctypes.c_int
         lib.gc_preset_params.argtypes = [ctypes.c_int, P, P, P, P]
         lib.gc_preset_params.restype = ctypes.c_int
         lib.gc_server_destroy.argtypes = [H]
@@ -250,6 +256,47 @@ def gc_color(offsets, idx, strategy="FF", X: int = 1, seed: int = 0, out=None, s
     _check(lib.gc_color(ctypes.byref(g), _strategy(strategy), int(X), int(seed) & (2**64 - 1),
                         _ptr(out), ctypes.byref(st), _stream(dev, stream)), "gc_color")
     return out, _stats_dict(st)
+
+
+ORDER = {"RANDOM": 0, "LF": 1, "LARGEST_FIRST": 1}
+
+
+def gc_color_ordered(offsets, idx, strategy="FF", X: int = 1, seed: int = 0, order="LF", out=None,
+                     stream=None):
+    """Speculative coloring with a vertex-visit order as the conflict priority
+    (Sec. 2.2.1): "LF" (largest degree wins) or "random" (= gc_color).
+    Returns (colors int32[n], stats dict)."""
+    lib = load()
+    g, keep = _graph(offsets, idx)
+    dev = keep[0].device
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.int32, device=dev)
+    _check_colors(out, g.n, dev, "out")
+    st = _Stats()
+    code = ORDER[order.upper()] if isinstance(order, str) else int(order)
+    _check(lib.gc_color_ordered(ctypes.byref(g), _strategy(strategy), int(X), int(seed) & (2**64 - 1),
+                                code, _ptr(out), ctypes.byref(st), _stream(dev, stream)),
+           "gc_color_ordered")
+    return out, _stats_dict(st)
+
+
+def gc_recolor_async(offsets, idx, colors_in, perm="RV", iterations: int = 1, seed: int = 0, out=None,
+                     stream=None):
+    """Asynchronous recoloring aRC (Sec. 3).  Returns (colors, ncolors list,
+    stats dict); stats["rounds"] sums the rounds of all iterations."""
+    lib = load()
+    g, keep = _graph(offsets, idx)
+    dev = keep[0].device
+    _check_colors(colors_in, g.n, dev, "colors_in")
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.int32, device=dev)
+    _check_colors(out, g.n, dev, "out")
+    nc = (ctypes.c_int32 * (iterations + 1))()
+    st = _Stats()
+    _check(lib.gc_recolor_async(ctypes.byref(g), _ptr(colors_in), _perm(perm), int(iterations),
+                                int(seed) & (2**64 - 1), _ptr(out), nc, ctypes.byref(st),
+                                _stream(dev, stream)), "gc_recolor_async")
+    return out, list(nc), _stats_dict(st)
 
 
 def gc_recolor(offsets, idx, colors_in, perm="RV", iterations: int = 1, seed: int = 0, out=None,

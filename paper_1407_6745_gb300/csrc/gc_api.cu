@@ -291,6 +291,44 @@ static gc_status gc_color_impl(const gc_graph* g, gc_strategy strategy, int32_t 
     return dc.unstage(colors_out, g->n, g->mem, s);
 }
 
+static gc_status gc_color_ordered_impl(const gc_graph* g, gc_strategy strategy, int32_t X, uint64_t seed,
+                                       gc_order order, int32_t* colors_out, gc_stats* stats, void* stream) {
+    if (order == GC_ORDER_RANDOM) return gc_color_impl(g, strategy, X, seed, colors_out, stats, stream);
+    if (order != GC_ORDER_LARGEST_FIRST) return GC_ERR_INVALID_ARG;
+    gc_status st = check_graph_args(g);
+    if (st != GC_OK) return st;
+    if (strategy != GC_FIRST_FIT && strategy != GC_RANDOM_X_FIT) return GC_ERR_INVALID_ARG;
+    if (strategy == GC_FIRST_FIT) X = 1;
+    if (X < 1) return GC_ERR_INVALID_ARG;
+    if (g->n > 0 && !colors_out) return GC_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceGraph dg;
+    DeviceColors dc;
+    if ((st = dg.stage(g, s)) != GC_OK) return st;
+    if ((st = dc.stage(colors_out, g->n, g->mem, false, s)) != GC_OK) return st;
+    st = color_lf_device(dg.g, X, seed, dc.d, stats, s);
+    if (st != GC_OK) return st;
+    return dc.unstage(colors_out, g->n, g->mem, s);
+}
+
+static gc_status gc_recolor_async_impl(const gc_graph* g, const int32_t* colors_in, gc_perm perm,
+                                       int32_t iterations, uint64_t seed, int32_t* colors_out,
+                                       int32_t* ncolors_per_iter, gc_stats* stats, void* stream) {
+    gc_status st = check_graph_args(g);
+    if (st != GC_OK) return st;
+    if (!perm_valid(perm) || iterations < 0) return GC_ERR_INVALID_ARG;
+    if (g->n > 0 && (!colors_in || !colors_out)) return GC_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceGraph dg;
+    DeviceColors din;
+    if ((st = dg.stage(g, s)) != GC_OK) return st;
+    if ((st = din.stage(const_cast<int32_t*>(colors_in), g->n, g->mem, true, s)) != GC_OK) return st;
+    int32_t* dout = g->mem == GC_MEM_HOST ? din.d : colors_out;
+    st = recolor_async_device(dg.g, din.d, perm, iterations, seed, dout, ncolors_per_iter, stats, s);
+    if (st != GC_OK) return st;
+    return din.unstage(colors_out, g->n, g->mem, s);
+}
+
 static gc_status gc_recolor_impl(const gc_graph* g, const int32_t* colors_in, gc_perm perm, int32_t iterations,
                      uint64_t seed, int32_t* colors_out, int32_t* ncolors_per_iter, gc_stats* stats,
                      void* stream) {
@@ -377,6 +415,22 @@ static gc_status gc_priorities_impl(uint64_t seed, int64_t n, uint32_t* out, voi
 gc_status gc_color(const gc_graph* g, gc_strategy strategy, int32_t X, uint64_t seed,
                    int32_t* colors_out, gc_stats* stats, void* stream) {
     const gc_status st = gc_color_impl(g, strategy, X, seed, colors_out, stats, stream);
+    prof_collect();
+    return st;
+}
+
+gc_status gc_color_ordered(const gc_graph* g, gc_strategy strategy, int32_t X, uint64_t seed,
+                           gc_order order, int32_t* colors_out, gc_stats* stats, void* stream) {
+    const gc_status st = gc_color_ordered_impl(g, strategy, X, seed, order, colors_out, stats, stream);
+    prof_collect();
+    return st;
+}
+
+gc_status gc_recolor_async(const gc_graph* g, const int32_t* colors_in, gc_perm perm,
+                           int32_t iterations, uint64_t seed, int32_t* colors_out,
+                           int32_t* ncolors_per_iter, gc_stats* stats, void* stream) {
+    const gc_status st = gc_recolor_async_impl(g, colors_in, perm, iterations, seed, colors_out,
+                                               ncolors_per_iter, stats, stream);
     prof_collect();
     return st;
 }

@@ -78,7 +78,19 @@ struct SpecArgs {
     int32_t* h_bwords;
     int32_t* pend;
     uint32_t* hbm;
+    // priority rule: 0 the random order; 1 Largest First (degree first);
+    // 2 aRC (rank of the vertex's previous class first, from prio_rank[prio_old[v]])
+    int32_t prio_kind;
+    const int32_t* prio_rank;
+    const int32_t* prio_old;
 };
+
+// A vertex-visit key (16 bits, clamped) above the upper half of the random
+// priority; equal keys still fall back to the id.
+__device__ __forceinline__ uint32_t ordered_prio(int64_t first_key, uint32_t p) {
+    const uint32_t k = static_cast<uint32_t>(first_key < 0 ? 0 : first_key > 65535 ? 65535 : first_key);
+    return (k << 16) | (p >> 16);
+}
 
 // Bitmap words of a heavy row: colors 1 .. 32 * words, at least deg + 64.
 __host__ __device__ __forceinline__ int32_t heavy_words(int32_t deg) { return (deg + 64) / 32 + 2; }
@@ -116,7 +128,10 @@ __global__ void __launch_bounds__(kBlock) k_spec_setup(SpecArgs a) {
         }
         const int b = bucket_of(deg, X, a.tune);
         a.bucket[v] = static_cast<uint8_t>(b);
-        a.key[v] = prio_of(seed, vl);  // tentative color 0
+        uint32_t p = prio_of(seed, vl);
+        if (a.prio_kind == 1) p = ordered_prio(deg, p);
+        else if (a.prio_kind == 2) p = ordered_prio(65535 - static_cast<int64_t>(a.prio_rank[a.prio_old[v]]), p);
+        a.key[v] = p;  // tentative color 0
         a.color[v] = 0;
         const unsigned act = __activemask();
         const unsigned peers = __match_any_sync(act, b);
@@ -627,9 +642,15 @@ gc_status rounds_in_graph(SpecArgs& a, int32_t X, int grid_t, int grid_c, cudaSt
 }
 
 // The speculative coloring; with graph_of / desc / win_round set, a batch.
+struct PrioRule {
+    int32_t kind = 0;
+    const int32_t* rank = nullptr;
+    const int32_t* old = nullptr;
+};
+
 static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int32_t* graph_of,
-                            const BatchDesc* desc, int32_t* win_round, int32_t* colors_out,
-                            gc_stats* stats, cudaStream_t s) {
+                            const BatchDesc* desc, int32_t* win_round, const PrioRule& rule,
+                            int32_t* colors_out, gc_stats* stats, cudaStream_t s) {
     if (g.n == 0) {
         if (stats) { std::memset(stats, 0, sizeof(*stats)); }
         return GC_OK;
@@ -656,6 +677,9 @@ static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int3
     a.graph_of = graph_of;
     a.desc = desc;
     a.win_round = win_round;
+    a.prio_kind = rule.kind;
+    a.prio_rank = rule.rank;
+    a.prio_old = rule.old;
 
     struct Events {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -749,7 +773,80 @@ static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int3
 
 gc_status color_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors_out,
                        gc_stats* stats, cudaStream_t s) {
-    return color_impl(g, X, seed, nullptr, nullptr, nullptr, colors_out, stats, s);
+    return color_impl(g, X, seed, nullptr, nullptr, nullptr, PrioRule{}, colors_out, stats, s);
+}
+
+gc_status color_lf_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors_out,
+                          gc_stats* stats, cudaStream_t s) {
+    PrioRule r;
+    r.kind = 1;
+    return color_impl(g, X, seed, nullptr, nullptr, nullptr, r, colors_out, stats, s);
+}
+
+// aRC (Sec. 3): every iteration colors the graph again by the speculative
+// First-Fit rounds, the vertices of earlier classes (in the iteration's
+// permutation of the previous coloring's classes) winning their conflicts.
+gc_status recolor_async_device(const Graph& g, const int32_t* colors_in, int32_t perm, int32_t iterations,
+                               uint64_t seed, int32_t* colors_out, int32_t* ncolors_per_iter,
+                               gc_stats* stats, cudaStream_t s) {
+    const int64_t n = g.n;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    Scratch sc_old;
+    if (!sc_old.alloc(n * 4, s)) return GC_ERR_OOM;
+    int32_t* old = sc_old.as<int32_t>();
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    gc_status st = GC_OK;
+    int32_t maxc = 0;
+    // the input: proper, and its max color (no iteration: copied through)
+    st = class_ranks_device(g, colors_in, false, perm, 0, seed, nullptr, &maxc, s);
+    if (st == GC_OK && ncolors_per_iter) ncolors_per_iter[0] = n > 0 ? maxc : 0;
+    const int32_t* cur = colors_in;
+    for (int32_t it = 0; it < iterations && st == GC_OK && n > 0; ++it) {
+        cudaError_t ce = cudaMemcpyAsync(old, cur, n * 4, cudaMemcpyDeviceToDevice, s);
+        if (ce != cudaSuccess) { st = cuda_status(ce); break; }
+        Scratch sc_rank;
+        if (!sc_rank.alloc((static_cast<int64_t>(maxc) + 1) * 4, s)) { st = GC_ERR_OOM; break; }
+        int32_t m = 0;
+        st = class_ranks_device(g, old, true, perm, it, seed, sc_rank.as<int32_t>(), &m, s);
+        if (st != GC_OK) break;
+        PrioRule r;
+        r.kind = 2;
+        r.rank = sc_rank.as<int32_t>();
+        r.old = old;
+        gc_stats cs;
+        st = color_impl(g, 1, seed, nullptr, nullptr, nullptr, r, colors_out, &cs, s);
+        if (st != GC_OK) break;
+        maxc = cs.max_color;
+        if (ncolors_per_iter) ncolors_per_iter[it + 1] = maxc;
+        if (stats) {
+            stats->rounds += cs.rounds;
+            stats->edges_examined += cs.edges_examined;
+            stats->conflicts += cs.conflicts;
+        }
+        cur = colors_out;
+    }
+    if (st == GC_OK && iterations == 0 && n > 0 && colors_out != colors_in) {
+        const cudaError_t ce = cudaMemcpyAsync(colors_out, colors_in, n * 4, cudaMemcpyDeviceToDevice, s);
+        if (ce != cudaSuccess) st = cuda_status(ce);
+    }
+    if (st == GC_OK && n == 0 && ncolors_per_iter)
+        for (int32_t i = 0; i <= iterations; ++i) ncolors_per_iter[i] = 0;
+    cudaEventRecord(e1, s);
+    const cudaError_t ce = cudaEventSynchronize(e1);
+    if (st == GC_OK && ce != cudaSuccess) st = cuda_status(ce);
+    if (stats) {
+        stats->iterations = iterations;
+        stats->max_color = maxc;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        stats->ms_recolor = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
 }
 
 // ---------------------------------------------------------------------------
@@ -854,7 +951,7 @@ gc_status color_batch_device(const Graph& g, const gc_batch_graph* graphs, int32
     const BatchDesc* d_desc = sd.as<BatchDesc>();
     int32_t* graph_of = sgo.as<int32_t>();
     batch_graph_of(g, d_desc, ng, graph_of, s);
-    st = color_impl(g, max_x, 0, graph_of, d_desc, swr.as<int32_t>(), colors_out, stats, s);
+    st = color_impl(g, max_x, 0, graph_of, d_desc, swr.as<int32_t>(), PrioRule{}, colors_out, stats, s);
     if (st != GC_OK) return st;
     if (rounds_out || max_color_out)
         st = batch_max_colors(g, graph_of, colors_out, swr.as<int32_t>(), ng, max_color_out, rounds_out, s);

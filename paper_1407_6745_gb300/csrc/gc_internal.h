@@ -97,6 +97,25 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
                          int32_t perm, int32_t iterations, uint64_t seed, int32_t* colors_out,
                          int32_t* ncolors_per_iter, gc_stats* stats, cudaStream_t s);
 
+// Speculative coloring where the larger degree wins a conflict (Largest
+// First as the first key of the priority, Sec. 2.2.1).
+gc_status color_lf_device(const Graph& g, int32_t X, uint64_t seed, int32_t* colors_out,
+                          gc_stats* stats, cudaStream_t s);
+
+// Asynchronous recoloring (aRC, Sec. 3) on device pointers; colors_out may
+// alias colors_in.  The input is validated.
+gc_status recolor_async_device(const Graph& g, const int32_t* colors_in, int32_t perm, int32_t iterations,
+                               uint64_t seed, int32_t* colors_out, int32_t* ncolors_per_iter,
+                               gc_stats* stats, cudaStream_t s);
+
+// The class permutation of iteration `iteration` of a proper coloring:
+// rank_out[c] (max color + 1 entries; nullptr: none) is the position of color
+// c in it, *maxc_out the max color.  Unless `trusted`, the coloring is
+// validated first (GC_ERR_IMPROPER_INPUT).
+gc_status class_ranks_device(const Graph& g, const int32_t* colors, bool trusted, int32_t perm,
+                             int32_t iteration, uint64_t seed, int32_t* rank_out, int32_t* maxc_out,
+                             cudaStream_t s);
+
 // Batches (see gc_batch_graph): descriptor checks, graph of each vertex,
 // per-graph statistics.
 gc_status batch_layout(const Graph& g, const gc_batch_graph* graphs, int32_t ng, int32_t* max_x);

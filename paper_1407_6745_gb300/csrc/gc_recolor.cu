@@ -160,6 +160,19 @@ __global__ void __launch_bounds__(kBlock) k_rc_validate(RcArgs a) {
     warp_max(&a.ctrl->max_in, my_max);
 }
 
+// Max color of a coloring known to be proper (colors outside [1, max input
+// color] still flag it improper).
+__global__ void __launch_bounds__(kBlock) k_rc_maxin(RcArgs a) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kBlock;
+    int32_t my_max = 0;
+    for (int64_t v = static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x; v < a.g.n; v += stride) {
+        const int32_t cv = a.old_c[v];
+        if (cv < 1 || cv > kMaxInputColor) atomicOr(&a.ctrl->err, kErrImproper);
+        else my_max = max(my_max, cv);
+    }
+    warp_max(&a.ctrl->max_in, my_max);
+}
+
 // ---------------------------------------------------------------------------
 // Histogram of (class, bucket); bucket-0 rows also count their chunks
 // ---------------------------------------------------------------------------
@@ -284,7 +297,7 @@ __global__ void __launch_bounds__(kOrderThreads) k_rc_order(RcArgs a) {
         k += total;
     }
     __syncthreads();
-    if (a.iteration == 0 && t == 0) a.ncolors[0] = k > 0 ? a.present[k - 1] : 0;
+    if (a.ncolors && a.iteration == 0 && t == 0) a.ncolors[0] = k > 0 ? a.present[k - 1] : 0;
 
     // the permutation (Sec. 3) of this iteration (Sec. 4.2.1 schedules)
     const int32_t perm = perm_at(a.perm, a.iteration);
@@ -681,6 +694,73 @@ __global__ void __launch_bounds__(kBlock, 5) k_rc_recolor_step(RcArgs a, int32_t
     warp_add(&a.ctrl->edges, edges);
     warp_max(&a.ncolors[a.iteration + 1], my_max);
     flush_next_hist(a, nh);
+}
+
+// ---------------------------------------------------------------------------
+// Class ranks of a coloring (for aRC): the histogram and permutation kernels
+// of one iteration, without the scatter and the class steps.
+// ---------------------------------------------------------------------------
+gc_status class_ranks_device(const Graph& g, const int32_t* colors, bool trusted, int32_t perm,
+                             int32_t iteration, uint64_t seed, int32_t* rank_out, int32_t* maxc_out,
+                             cudaStream_t s) {
+    const int64_t n = g.n;
+    *maxc_out = 0;
+    if (n == 0) return GC_OK;
+    const Tuning tune = current_tuning();
+    const int grid = persistent_grid(tune);
+    const int vgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, grid)));
+    Scratch sc_ctrl, sc_bucket;
+    if (!sc_ctrl.alloc(sizeof(RcCtrl), s) || !sc_bucket.alloc(n + 1, s)) return GC_ERR_OOM;
+    RcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.tune = tune;
+    a.seed = seed;
+    a.perm = perm;
+    a.iteration = iteration;
+    a.old_c = colors;
+    a.bucket = sc_bucket.as<uint8_t>();
+    a.ctrl = sc_ctrl.as<RcCtrl>();
+    cudaMemsetAsync(a.ctrl, 0, sizeof(RcCtrl), s);
+    GC_LAUNCH(KID_RC_BUCKET, s, k_rc_bucket<<<vgrid, kBlock, 0, s>>>(a));
+    if (!trusted) GC_LAUNCH(KID_RC_VALIDATE, s, k_rc_validate<<<grid, kBlock, 0, s>>>(a));
+    else GC_LAUNCH(KID_RC_VALIDATE, s, k_rc_maxin<<<vgrid, kBlock, 0, s>>>(a));
+    RcCtrl h;
+    cudaError_t ce = cudaMemcpyAsync(&h, a.ctrl, sizeof(RcCtrl), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    if (h.err & kErrBadGraph) return GC_ERR_BAD_GRAPH;
+    if (h.err & kErrImproper) return GC_ERR_IMPROPER_INPUT;
+    *maxc_out = h.max_in;
+    if (!rank_out) return GC_OK;
+    const int32_t cap = std::max(h.max_in, 1);
+    const int64_t ent = static_cast<int64_t>(cap + 1) * kNB;
+    Scratch sc_cls, sc_units, sc_present, sc_psize, sc_order, sc_jtab, sc_seg, sc_tiles, sc_fill;
+    if (!sc_cls.alloc(ent * 4, s) || !sc_units.alloc((cap + 1) * 4, s) ||
+        !sc_present.alloc((cap + 1) * 4, s) || !sc_psize.alloc((cap + 1) * 4, s) ||
+        !sc_order.alloc((cap + 1) * 4, s) || !sc_jtab.alloc((cap + 1) * 4, s) ||
+        !sc_seg.alloc((ent + 1) * 4, s) || !sc_tiles.alloc((ent + 1) * 4, s) || !sc_fill.alloc(ent * 4, s))
+        return GC_ERR_OOM;
+    a.cap = cap;
+    a.cls_cnt = sc_cls.as<int32_t>();
+    a.cls_units = sc_units.as<int32_t>();
+    a.present = sc_present.as<int32_t>();
+    a.psize = sc_psize.as<int32_t>();
+    a.order = sc_order.as<int32_t>();
+    a.jtab = sc_jtab.as<int32_t>();
+    a.rank_of = rank_out;
+    a.seg_start = sc_seg.as<int32_t>();
+    a.tile_prefix = sc_tiles.as<int32_t>();
+    a.fill = sc_fill.as<int32_t>();
+    cudaMemsetAsync(a.cls_cnt, 0, ent * 4, s);
+    cudaMemsetAsync(a.cls_units, 0, (cap + 1) * 4, s);
+    cudaMemsetAsync(rank_out, 0, (cap + 1) * 4, s);
+    GC_LAUNCH(KID_RC_HIST, s, k_rc_hist<<<vgrid, kBlock, 0, s>>>(a));
+    GC_LAUNCH(KID_RC_ORDER, s, k_rc_order<<<1, kOrderThreads, 0, s>>>(a));
+    ce = cudaMemcpyAsync(&h, a.ctrl, sizeof(RcCtrl), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_status(ce);
+    return status_from_err_bits(h.err);
 }
 
 // ---------------------------------------------------------------------------
