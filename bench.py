@@ -58,6 +58,15 @@ WORKLOADS = {
                           perm_seed=5,
                           label="R-MAT scale 24 ef 16 (0.57,0.19,0.19,0.05) seed 4; First Fit + 20 "
                                 "recoloring iterations ND-RAND%2^i (seed 5)"),
+    "rmat-er": dict(graph="rmat-er", strategy="FF", X=1, seed=7, perm="ND", iterations=10, perm_seed=0,
+                    label="RMAT-ER of Table 2: scale 24, edge factor 8, (0.25,0.25,0.25,0.25) seed 4; "
+                          "First Fit + 10 ND iterations"),
+    "rmat-good": dict(graph="rmat-good", strategy="FF", X=1, seed=7, perm="ND", iterations=10, perm_seed=0,
+                      label="RMAT-Good of Table 2: scale 24, edge factor 8, (0.45,0.15,0.15,0.25) seed 4; "
+                            "First Fit + 10 ND iterations"),
+    "rmat-bad": dict(graph="rmat-bad", strategy="FF", X=1, seed=7, perm="ND", iterations=10, perm_seed=0,
+                     label="RMAT-Bad of Table 2: scale 24, edge factor 8, (0.55,0.15,0.15,0.15) seed 4; "
+                           "First Fit + 10 ND iterations"),
     "batch": dict(label="batch"),
     "serve": dict(label="serve"),
     "er10k": dict(graph="er10k", strategy="FF", X=1, seed=1, perm="RV", iterations=2, perm_seed=0,

@@ -331,17 +331,28 @@ def batch_mix(count: int, seed: int, n_lo: float, n_hi: float, device="cpu"):
 # The benchmark workloads
 # ---------------------------------------------------------------------------
 
+# The (a, b, c) quadrant probabilities of the paper's R-MAT graphs (Sec. 4.1).
+PAPER_RMAT = {"er": (0.25, 0.25, 0.25), "good": (0.45, 0.15, 0.15), "bad": (0.55, 0.15, 0.15)}
+
+
 def workload(name: str, device="cpu") -> CSRGraph:
     """The named synthetic workloads:
     er10k    -- G(n=10,000, mean degree 16), seed 1
     st27-128 -- 27-point stencil 128^3, ids shuffled by a seed-2 permutation
     rmat24   -- R-MAT scale 24, edge factor 16, (0.57, 0.19, 0.19, 0.05), seed 4
-    Smaller variants for tests: st27-<side>, rmat<scale>."""
+    rmat-er / rmat-good / rmat-bad -- the R-MAT classes of Sec. 4.1 (Table 2):
+                (0.25, 0.25, 0.25, 0.25), (0.45, 0.15, 0.15, 0.25) and
+                (0.55, 0.15, 0.15, 0.15), scale 24, edge factor 8, seed 4
+    Smaller variants for tests: st27-<side>, rmat<scale>, rmat-er<scale>, ..."""
     if name == "er10k":
         return erdos_renyi(10_000, 16.0, seed=1, device=device)
     if name.startswith("st27-"):
         s = int(name.split("-")[1])
         return shuffle_ids(stencil_3d(s, s, s, 27, device=device), seed=2)
+    for cls, (a, b, c) in PAPER_RMAT.items():
+        if name.startswith(f"rmat-{cls}"):
+            rest = name[len(f"rmat-{cls}"):]
+            return rmat(int(rest) if rest else 24, 8, a, b, c, seed=4, device=device)
     if name.startswith("rmat"):
         scale = int(name[4:])
         return rmat(scale, 16, 0.57, 0.19, 0.19, seed=4, device=device)

@@ -110,6 +110,8 @@ def _load():
         lib.oracle_recolor_async.restype = ctypes.c_int
         lib.oracle_ordered_priority.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64]
         lib.oracle_ordered_priority.restype = ctypes.c_uint32
+        lib.oracle_greedy_sequential.argtypes = [ctypes.c_int64, P, P, ctypes.c_int32, P]
+        lib.oracle_greedy_sequential.restype = ctypes.c_int
         lib.oracle_perm_of_iteration.argtypes = [ctypes.c_int32, ctypes.c_int32]
         lib.oracle_perm_of_iteration.restype = ctypes.c_int32
         for f in (lib.oracle_color, lib.oracle_color_tables, lib.oracle_validate,
@@ -253,6 +255,18 @@ def recolor_async(off, idx, colors_in, perm="RV", iterations: int = 1, seed: int
     if rc != OK:
         raise OracleError(rc, "recolor_async")
     return out, nc, rounds[:iterations]
+
+
+def greedy_sequential(off, idx, order="NAT"):
+    """Sequential Alg. 1 in the Natural ("NAT", id) or Largest-First ("LF",
+    non-increasing degree, ties by id) vertex-visit order."""
+    lib = _load()
+    off, idx, n = _graph(off, idx)
+    out = np.zeros(n, dtype=np.int32)
+    rc = lib.oracle_greedy_sequential(n, _ptr(off), _ptr(idx), {"NAT": 0, "LF": 1}[order.upper()], _ptr(out))
+    if rc != OK:
+        raise OracleError(rc, "greedy_sequential")
+    return out
 
 
 def recolor(off, idx, colors_in, perm="RV", iterations: int = 1, seed: int = 0):

@@ -674,3 +674,55 @@ done:
     free(old); free(nw); free(prio); free(size); free(order); free(rank);
     return status;
 }
+
+/* ------------------------------------------------------------------ */
+/* Sequential greedy (Alg. 1, Sec. 2.1) in a vertex-visit order         */
+/* (Sec. 2.2.1): Natural (id order) or Largest First (non-increasing    */
+/* degree, equal degrees in id order).  The columns NAT and LF of       */
+/* Tables 1 and 2.                                                      */
+/* ------------------------------------------------------------------ */
+
+int oracle_greedy_sequential(int64_t n, const int64_t* off, const int32_t* idx, int32_t order_kind,
+                             int32_t* colors_out)
+{
+    int64_t *order = NULL, *forbidden = NULL, *count = NULL;
+    int64_t v, e, i, maxd, d;
+    int status;
+    if (order_kind != 0 && order_kind != 1) return OR_ERR_INVALID_ARG;
+    status = check_graph(n, off, idx);
+    if (status != OR_OK) return status;
+    if (n == 0) return OR_OK;
+    maxd = max_degree(n, off);
+    order = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    forbidden = (int64_t*)malloc(sizeof(int64_t) * (size_t)(maxd + 2));
+    count = (int64_t*)calloc((size_t)maxd + 2, sizeof(int64_t));
+    if (!order || !forbidden || !count) { status = OR_ERR_OOM; goto done; }
+    if (order_kind == 0) {
+        for (v = 0; v < n; ++v) order[v] = v;
+    } else {
+        /* counting sort by degree, largest first, stable in id */
+        for (v = 0; v < n; ++v) count[off[v + 1] - off[v]]++;
+        {
+            int64_t pos = 0;
+            for (d = maxd; d >= 0; --d) { int64_t c = count[d]; count[d] = pos; pos += c; }
+        }
+        for (v = 0; v < n; ++v) order[count[off[v + 1] - off[v]]++] = v;
+    }
+    for (i = 0; i <= maxd + 1; ++i) forbidden[i] = -1;
+    for (v = 0; v < n; ++v) colors_out[v] = 0;
+    for (i = 0; i < n; ++i) {
+        int32_t c;
+        v = order[i];
+        for (e = off[v]; e < off[v + 1]; ++e) {
+            int32_t cu = colors_out[idx[e]];
+            if (cu > 0) forbidden[cu] = v;
+        }
+        c = 1;
+        while (forbidden[c] == v) ++c;
+        colors_out[v] = c;
+    }
+    status = OR_OK;
+done:
+    free(order); free(forbidden); free(count);
+    return status;
+}

@@ -465,6 +465,48 @@ def test_arc_properness_bounds_and_rounds(seed):
 
 
 # --------------------------------------------------------------------------
+# Sequential greedy in the NAT and LF orders (Alg. 1; Tables 1-2 columns)
+# --------------------------------------------------------------------------
+
+def _crown(k):
+    """K_{k,k} minus a perfect matching, sides interleaved u1, v1, u2, v2, ...:
+    the classic graph on which natural-order greedy uses k colors (chi = 2)."""
+    edges = [(2 * i, 2 * j + 1) for i in range(k) for j in range(k) if i != j]
+    return gg.from_edge_list(2 * k, edges)
+
+
+@pytest.mark.parametrize("k", [3, 5, 9])
+def test_greedy_natural_order_on_crown_graph(k):
+    off, idx = _np(_crown(k))
+    c = oracle.greedy_sequential(off, idx, "NAT")
+    assert c.max() == k and list(c[0::2]) == list(range(1, k + 1))
+    assert oracle.greedy_sequential(off, idx, "LF").max() == k  # all degrees equal: id order
+
+
+def test_greedy_closed_forms():
+    off, idx = _np(gg.star(30))
+    assert list(oracle.greedy_sequential(off, idx, "NAT")[:3]) == [1, 2, 2]
+    off, idx = _np(gg.complete(12))
+    assert sorted(oracle.greedy_sequential(off, idx, "LF")) == list(range(1, 13))
+    off, idx = _np(gg.path(7))
+    assert list(oracle.greedy_sequential(off, idx, "NAT")) == [1, 2, 1, 2, 1, 2, 1]
+    # LF on a path: the interior (degree 2) first, in id order, then the ends
+    assert list(oracle.greedy_sequential(off, idx, "LF")) == [2, 1, 2, 1, 2, 1, 2]
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_greedy_bounds(seed):
+    n = 4 + seed % 7
+    g = gg.random_small(n, 0.5, seed)
+    off, idx = _np(g)
+    chi = _brute_chromatic(n, off, idx)
+    for order in ("NAT", "LF"):
+        c = oracle.greedy_sequential(off, idx, order)
+        assert oracle.validate(off, idx, c)["n_conflicts"] == 0
+        assert chi <= c.max() <= _deg(off).max(initial=0) + 1
+
+
+# --------------------------------------------------------------------------
 # Class orders and the generator
 # --------------------------------------------------------------------------
 
