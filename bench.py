@@ -67,6 +67,18 @@ WORKLOADS = {
     "rmat-bad": dict(graph="rmat-bad", strategy="FF", X=1, seed=7, perm="ND", iterations=10, perm_seed=0,
                      label="RMAT-Bad of Table 2: scale 24, edge factor 8, (0.55,0.15,0.15,0.15) seed 4; "
                            "First Fit + 10 ND iterations"),
+    "st27-128-lf": dict(graph="st27-128", kind="lf", strategy="RXF", X=8, seed=3, perm="NI", iterations=10,
+                        perm_seed=0,
+                        label="27-point stencil 128^3, ids shuffled (seed 2); Random-8 Fit with "
+                              "Largest-First priorities (seed 3) + 10 NI iterations"),
+    "st27-128-arc": dict(graph="st27-128", kind="arc", strategy="RXF", X=8, seed=3, perm="ND", iterations=10,
+                         perm_seed=0,
+                         label="27-point stencil 128^3, ids shuffled (seed 2); Random-8 Fit (seed 3) + "
+                               "10 asynchronous recoloring (aRC) iterations ND"),
+    "rmat24-arc": dict(graph="rmat24", kind="arc", strategy="FF", X=1, seed=7, perm="ND", iterations=5,
+                       perm_seed=0,
+                       label="R-MAT scale 24 ef 16 (0.57,0.19,0.19,0.05) seed 4; First Fit + 5 "
+                             "asynchronous recoloring (aRC) iterations ND"),
     "batch": dict(label="batch"),
     "serve": dict(label="serve"),
     "er10k": dict(graph="er10k", strategy="FF", X=1, seed=1, perm="RV", iterations=2, perm_seed=0,
@@ -178,10 +190,40 @@ def _oracle_sample(g, wl, passes_recolor):
     off, idx = g.numpy()
     t0 = time.perf_counter()
     X = wl["X"] if wl["strategy"] == "RXF" else 1
-    c, _ = oracle.color(off, idx, X, wl["seed"])
+    kind = wl.get("kind", "rc")
+    if kind == "lf":
+        c, _ = oracle.color_lf(off, idx, X, wl["seed"])
+    else:
+        c, _ = oracle.color(off, idx, X, wl["seed"])
     if passes_recolor:
-        c, _ = oracle.recolor(off, idx, c, wl["perm"], passes_recolor, wl["perm_seed"])
+        if kind == "arc":
+            c, _, _ = oracle.recolor_async(off, idx, c, wl["perm"], passes_recolor, wl["perm_seed"])
+        else:
+            c, _ = oracle.recolor(off, idx, c, wl["perm"], passes_recolor, wl["perm_seed"])
     return time.perf_counter() - t0, c, 1 + passes_recolor
+
+
+def _run_path(gc, off, idx, wl, out):
+    """One pass of the workload's path through the C ABI: the coloring, the
+    recoloring iterations and the validation.  Returns (colors, ncolors per
+    iteration, stats, validation)."""
+    kind = wl.get("kind", "rc")
+    if kind == "rc":
+        return gc.gc_color_recolor(off, idx, wl["strategy"], wl["X"], wl["seed"], wl["perm"],
+                                   wl["iterations"], wl["perm_seed"], out=out, validate=True)
+    if kind == "lf":
+        c, st = gc.gc_color_ordered(off, idx, wl["strategy"], wl["X"], wl["seed"], "LF", out=out)
+        _, nc, rs = gc.gc_recolor(off, idx, c, wl["perm"], wl["iterations"], wl["perm_seed"], out=out)
+    else:
+        c, st = gc.gc_color(off, idx, wl["strategy"], wl["X"], wl["seed"], out=out)
+        _, nc, rs = gc.gc_recolor_async(off, idx, c, wl["perm"], wl["iterations"], wl["perm_seed"], out=out)
+    st = dict(st)
+    st["edges_examined"] += rs["edges_examined"]
+    st["iterations"] = wl["iterations"]
+    if kind == "arc":
+        st["rounds_recolor"] = rs["rounds"]
+        st["conflicts_recolor"] = rs["conflicts"]
+    return out, nc, st, gc.gc_validate(off, idx, out)
 
 
 def run_reference(args, wl, g):
@@ -503,8 +545,7 @@ def main():
     passes = 1 + wl["iterations"]
 
     def step():
-        return gc.gc_color_recolor(off, idx, wl["strategy"], wl["X"], wl["seed"], wl["perm"],
-                                   wl["iterations"], wl["perm_seed"], out=out, validate=True)
+        return _run_path(gc, off, idx, wl, out)
 
     def barrier():
         if ws > 1:
@@ -546,15 +587,33 @@ def main():
     top = max(prof.items(), key=lambda kv: kv[1][1])
     top_name, (top_launches, top_ms) = top
     per_launch_ms = top_ms / top_launches
-    # algorithmic (compulsory) bytes per launch of the dominant kernel
+    # algorithmic bytes per launch of the dominant kernel: its bytes per step
+    # (the units it processes x the bytes per unit) over its launches per step
+    launches_per_step = top_launches / prof_steps
+    kind = wl.get("kind", "rc")
     if top_name in ("k_rc_recolor_coop", "k_rc_recolor_step"):
-        units = f"one recoloring iteration: every vertex once, nnz={nnz} entries"
-        alg_bytes = 4 * nnz + 16 * n
+        # per recoloring iteration: every adjacency id once (4 B) and every
+        # vertex's 16-byte work item once
+        per_step = wl["iterations"] * (4 * nnz + 16 * n)
+        units = (f"recoloring iterations: 4 B per adjacency id + 16 B per vertex work item, "
+                 f"{wl['iterations']} x (4*{nnz} + 16*{n}) B per step over "
+                 f"{launches_per_step:g} launches")
+    elif top_name in ("spec_rounds_graph", "k_tentative", "k_conflict"):
+        # speculative rounds: per round and work-set vertex, its row's ids in
+        # both phases (4 B per examined entry) and its 16-byte work item in
+        # both phases; edges_examined and conflicts count exactly those
+        spec_edges = pstats["edges_examined"] - (wl["iterations"] * nnz if kind != "arc" else 0)
+        colorings = 1 + (wl["iterations"] if kind == "arc" else 0)
+        visits = colorings * n + pstats["conflicts"] + pstats.get("conflicts_recolor", 0)
+        per_step = 4 * spec_edges + 32 * visits
+        if top_name != "spec_rounds_graph":
+            per_step /= 2  # one of the two phases
+        units = ("speculative rounds: 4 B per examined adjacency entry + 32 B per work-set visit "
+                 f"(both phases), {per_step:.4g} B per step over {launches_per_step:g} launches")
     else:
-        visited = (pstats["conflicts"] + n)  # vertex visits over all rounds
-        scanned = pstats["edges_examined"] - wl["iterations"] * nnz  # both phases
-        alg_bytes = (4 * scanned / 2 + 16 * visited) / pstats["rounds"]
-        units = "one speculative round (average over the rounds of a step)"
+        per_step = None
+        units = "no algorithmic byte count for this kernel"
+    alg_bytes = per_step / launches_per_step if per_step is not None else 0.0
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
     peak, peak_kind = _peak_hbm()
     roofline = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak,
@@ -573,9 +632,7 @@ def main():
         out_h = torch.empty(n, dtype=torch.int32).pin_memory()
 
         def hstep():
-            return gc.gc_color_recolor(off_h, idx_h, wl["strategy"], wl["X"], wl["seed"],
-                                       wl["perm"], wl["iterations"], wl["perm_seed"], out=out_h,
-                                       validate=True)
+            return _run_path(gc, off_h, idx_h, wl, out_h)
         hstep()
         barrier()
         torch.cuda.synchronize(dev)

@@ -50,6 +50,18 @@ struct SpecCtrl {
     long long heavy_words;    // bitmap words over all heavy rows
 };
 
+// Heavy rows (bucket 0): index of each, its pending list (start, length;
+// length -1 until first built: the row itself) and forbidden bitmap.
+struct HeavyRows {
+    int32_t* hid;
+    int64_t* h_pbeg;
+    int32_t* h_pcnt;
+    int64_t* h_bbeg;
+    int32_t* h_bwords;
+    int32_t* pend;
+    uint32_t* hbm;
+};
+
 struct SpecArgs {
     Graph g;
     int32_t X;
@@ -69,15 +81,9 @@ struct SpecArgs {
     const int32_t* graph_of;
     const BatchDesc* desc;
     int32_t* win_round;
-    // heavy rows (bucket 0): index of each, its pending list (start, length;
-    // length -1 until first built: the row itself) and forbidden bitmap
-    int32_t* hid;
-    int64_t* h_pbeg;
-    int32_t* h_pcnt;
-    int64_t* h_bbeg;
-    int32_t* h_bwords;
-    int32_t* pend;
-    uint32_t* hbm;
+    // heavy rows (bucket 0), in device memory so that the arrays can be
+    // sized after the CUDA graph of the rounds has been built
+    struct HeavyRows* heavy;
     // priority rule: 0 the random order; 1 Largest First (degree first);
     // 2 aRC (rank of the vertex's previous class first, from prio_rank[prio_old[v]])
     int32_t prio_kind;
@@ -219,11 +225,12 @@ __global__ void __launch_bounds__(kHeavyThreads) k_heavy_setup(SpecArgs a, int32
             tw += s_w[k];
         }
         if (h < nh) {
-            a.hid[v] = h;
-            a.h_pbeg[h] = be + ie - e;
-            a.h_pcnt[h] = -1;
-            a.h_bbeg[h] = bw + iw - wd;
-            a.h_bwords[h] = static_cast<int32_t>(wd);
+            const HeavyRows& hr = *a.heavy;
+            hr.hid[v] = h;
+            hr.h_pbeg[h] = be + ie - e;
+            hr.h_pcnt[h] = -1;
+            hr.h_bbeg[h] = bw + iw - wd;
+            hr.h_bwords[h] = static_cast<int32_t>(wd);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -313,13 +320,14 @@ __device__ __forceinline__ void tentative_group_tile(const SpecArgs& a, const Ro
 // colors (Random-X with a large X) the row is scanned in full instead.
 __device__ int32_t choose_heavy(const SpecArgs& a, const WorkItem& it, uint32_t j, SpecShared& sm) {
     const int t = threadIdx.x, l = lane_id(), w = t >> 5;
-    const int32_t h = a.hid[it.v];
-    const int32_t pc = a.h_pcnt[h];
+    const HeavyRows hr = *a.heavy;
+    const int32_t h = hr.hid[it.v];
+    const int32_t pc = hr.h_pcnt[h];
     const int64_t cnt = pc < 0 ? static_cast<int64_t>(it.deg) : static_cast<int64_t>(pc);
-    const int32_t* src = pc < 0 ? a.g.idx + it.beg : a.pend + a.h_pbeg[h];
-    int32_t* dst = a.pend + a.h_pbeg[h];
-    uint32_t* bm = a.hbm + a.h_bbeg[h];
-    const int32_t words = a.h_bwords[h];
+    const int32_t* src = pc < 0 ? a.g.idx + it.beg : hr.pend + hr.h_pbeg[h];
+    int32_t* dst = hr.pend + hr.h_pbeg[h];
+    uint32_t* bm = hr.hbm + hr.h_bbeg[h];
+    const int32_t words = hr.h_bwords[h];
     const uint32_t bits = 32u * static_cast<uint32_t>(words);
     int32_t kept = 0;
     for (int64_t i0 = 0; i0 < cnt; i0 += kBlock) {
@@ -351,7 +359,7 @@ __device__ int32_t choose_heavy(const SpecArgs& a, const WorkItem& it, uint32_t 
         kept += total;
         __syncthreads();
     }
-    if (t == 0) a.h_pcnt[h] = kept;
+    if (t == 0) hr.h_pcnt[h] = kept;
     // the j-th free bit of the bitmap (bit b = color b + 1); L2 reads, since
     // the block's own atomics went there
     for (int32_t w0 = 0; w0 < words; w0 += kBlock) {
@@ -461,9 +469,10 @@ __device__ __forceinline__ bool loses(const SpecArgs& a, const WorkItem& it, int
 // neighbors uncolored before the round, the only ones that can share its
 // tentative color.
 __device__ __forceinline__ bool loses_pending(const SpecArgs& a, const WorkItem& it) {
-    const int32_t h = a.hid[it.v];
-    const int32_t pc = a.h_pcnt[h];
-    const int32_t* lst = a.pend + a.h_pbeg[h];
+    const HeavyRows hr = *a.heavy;
+    const int32_t h = hr.hid[it.v];
+    const int32_t pc = hr.h_pcnt[h];
+    const int32_t* lst = hr.pend + hr.h_pbeg[h];
     const unsigned long long* key = reinterpret_cast<const unsigned long long*>(a.key);
     const uint64_t kv = __ldg(key + it.v);
     const uint32_t tv = static_cast<uint32_t>(kv >> 32);
@@ -595,9 +604,18 @@ thread_local PinnedWord t_pinned;
 // The rounds as one CUDA graph: a WHILE node whose body is {tentative,
 // conflict}; the last block of the conflict kernel sets the condition from
 // the size of the next work set, so no round waits for the host.
-gc_status rounds_in_graph(SpecArgs& a, int32_t X, int grid_t, int grid_c, cudaStream_t s) {
+struct RoundsGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    ~RoundsGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+gc_status build_rounds_graph(const SpecArgs& a, int32_t X, int grid_t, int grid_c, RoundsGraph& rg) {
+    cudaGraph_t& graph = rg.graph;
+    cudaGraphExec_t& exec = rg.exec;
     cudaError_t e = cudaGraphCreate(&graph, 0);
     cudaGraphConditionalHandle handle = 0;
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
@@ -630,14 +648,14 @@ gc_status rounds_in_graph(SpecArgs& a, int32_t X, int grid_t, int grid_c, cudaSt
         if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &k2);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e == cudaSuccess) {
-        prof_begin(KID_SPEC_GRAPH, s);
-        e = cudaGraphLaunch(exec, s);
-        prof_end(KID_SPEC_GRAPH, s);
-    }
+    return cuda_status(e);
+}
+
+gc_status launch_rounds_graph(RoundsGraph& rg, cudaStream_t s) {
+    prof_begin(KID_SPEC_GRAPH, s);
+    cudaError_t e = cudaGraphLaunch(rg.exec, s);
+    prof_end(KID_SPEC_GRAPH, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
     return cuda_status(e);
 }
 
@@ -699,9 +717,18 @@ static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int3
     const int grid_c = resident_grid(k_conflict, a.tune);
     const int setup_grid = static_cast<int>(
         std::min<int64_t>((n + kBlock - 1) / kBlock, resident_grid(k_spec_setup, a.tune)));
+    Scratch sc_heavy;
+    if (!sc_heavy.alloc(sizeof(HeavyRows), s)) return GC_ERR_OOM;
+    a.heavy = sc_heavy.as<HeavyRows>();
+    cudaMemsetAsync(a.heavy, 0, sizeof(HeavyRows), s);
     GC_LAUNCH(KID_SPEC_SETUP, s, k_spec_setup<<<setup_grid, kBlock, 0, s>>>(a));
     GC_LAUNCH(KID_SPEC_FILL, s, k_spec_fill<<<setup_grid, kBlock, 0, s>>>(a));
-    // heavy rows: their pending lists and bitmaps (sizes read back once)
+    gc_status st = GC_OK;
+    a.round_limit = static_cast<int32_t>(std::min<int64_t>(n + 2, INT32_MAX));
+    // the rounds' CUDA graph is built while the set-up kernels run
+    RoundsGraph rg;
+    if (a.tune.spec_graph && (st = build_rounds_graph(a, X, grid_t, grid_c, rg)) != GC_OK) return st;
+    // heavy rows: their pending lists and bitmaps (sizes read back)
     Scratch sc_hid, sc_pbeg, sc_pcnt, sc_bbeg, sc_bwords, sc_pend, sc_hbm;
     {
         SpecCtrl h0;
@@ -715,11 +742,14 @@ static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int3
                 !sc_pcnt.alloc(static_cast<int64_t>(nh) * 4, s) || !sc_bbeg.alloc(static_cast<int64_t>(nh) * 8, s) ||
                 !sc_bwords.alloc(static_cast<int64_t>(nh) * 4, s))
                 return GC_ERR_OOM;
-            a.hid = sc_hid.as<int32_t>();
-            a.h_pbeg = sc_pbeg.as<int64_t>();
-            a.h_pcnt = sc_pcnt.as<int32_t>();
-            a.h_bbeg = sc_bbeg.as<int64_t>();
-            a.h_bwords = sc_bwords.as<int32_t>();
+            HeavyRows hr1{};
+            hr1.hid = sc_hid.as<int32_t>();
+            hr1.h_pbeg = sc_pbeg.as<int64_t>();
+            hr1.h_pcnt = sc_pcnt.as<int32_t>();
+            hr1.h_bbeg = sc_bbeg.as<int64_t>();
+            hr1.h_bwords = sc_bwords.as<int32_t>();
+            ce = cudaMemcpyAsync(a.heavy, &hr1, sizeof(HeavyRows), cudaMemcpyHostToDevice, s);
+            if (ce != cudaSuccess) return cuda_status(ce);
             GC_LAUNCH(KID_SPEC_FILL, s, k_heavy_setup<<<1, kHeavyThreads, 0, s>>>(a, nh));
             ce = cudaMemcpyAsync(&h0, a.ctrl, sizeof(SpecCtrl), cudaMemcpyDeviceToHost, s);
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -727,16 +757,18 @@ static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int3
             if (!sc_pend.alloc(static_cast<size_t>(h0.heavy_entries) * 4, s) ||
                 !sc_hbm.alloc(static_cast<size_t>(h0.heavy_words) * 4, s))
                 return GC_ERR_OOM;
-            a.pend = sc_pend.as<int32_t>();
-            a.hbm = sc_hbm.as<uint32_t>();
-            ce = cudaMemsetAsync(a.hbm, 0, static_cast<size_t>(h0.heavy_words) * 4, s);
+            HeavyRows hr2 = hr1;
+            hr2.pend = sc_pend.as<int32_t>();
+            hr2.hbm = sc_hbm.as<uint32_t>();
+            ce = cudaMemsetAsync(hr2.hbm, 0, static_cast<size_t>(h0.heavy_words) * 4, s);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(a.heavy, &hr2, sizeof(HeavyRows), cudaMemcpyHostToDevice, s);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
             if (ce != cudaSuccess) return cuda_status(ce);
         }
     }
-    gc_status st = GC_OK;
-    a.round_limit = static_cast<int32_t>(std::min<int64_t>(n + 2, INT32_MAX));
     if (a.tune.spec_graph) {
-        st = rounds_in_graph(a, X, grid_t, grid_c, s);
+        st = launch_rounds_graph(rg, s);
     } else {
         int32_t rounds = 0;
         for (;;) {
