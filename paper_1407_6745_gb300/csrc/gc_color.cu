@@ -137,7 +137,10 @@ __global__ void __launch_bounds__(kBlock) k_spec_setup(SpecArgs a) {
         uint32_t p = prio_of(seed, vl);
         if (a.prio_kind == 1) p = ordered_prio(deg, p);
         else if (a.prio_kind == 2) p = ordered_prio(65535 - static_cast<int64_t>(a.prio_rank[a.prio_old[v]]), p);
-        a.key[v] = p;  // tentative color 0
+        // round 0's tentative color: nothing is colored yet, so the j-th
+        // permissible color is j + 1 (First Fit: 1)
+        const uint32_t j0 = (a.graph_of || a.X > 1) ? draw_index(a, v, 0) : 0u;
+        a.key[v] = (static_cast<uint64_t>(j0 + 1u) << 32) | p;
         a.color[v] = 0;
         const unsigned act = __activemask();
         const unsigned peers = __match_any_sync(act, b);
@@ -398,6 +401,11 @@ __global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
     const int par = round & 1;
     const WorkItem* list = par ? a.list1 : a.list0;
     if (blockIdx.x == 0 && threadIdx.x < kNB) a.ctrl->cnt[par ^ 1][threadIdx.x] = 0;
+    if (round == 0) {  // tentative colors set with the priorities (every row counted once)
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            atomicAdd(&a.ctrl->edges, static_cast<unsigned long long>(a.g.nnz));
+        return;
+    }
     load_round_tiles(a.ctrl, par, rt);
     unsigned long long edges = 0;
     const SnapshotFetch fetch{a.color};
@@ -408,8 +416,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
         case 0: {
             const WorkItem it = load_item(list + rt.start[0] + first);
             const uint32_t j = kRXF ? draw_index(a, it.v, round) : 0u;
-            // round 0: nothing is colored yet, so the j-th permissible color is j + 1
-            int32_t c = round == 0 ? static_cast<int32_t>(j) + 1 : choose_heavy(a, it, j, sm);
+            int32_t c = choose_heavy(a, it, j, sm);  // rounds >= 1
             if (c < 0) c = choose_block<4>(a.g, it.beg, it.deg, j, fetch, sm.blk, &a.ctrl->err);
             if (threadIdx.x == 0) {
                 set_tent(a, it.v, c);
