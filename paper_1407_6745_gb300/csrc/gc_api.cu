@@ -88,18 +88,24 @@ int sm_count() {
     return g_sms[dev];
 }
 
-int occupancy_of(const void* kernel, int threads) {
+int occupancy_of(const void* kernel, int threads, size_t dyn_smem) {
+    struct Entry {
+        const void* k;
+        int dev;
+        size_t dyn;
+        int nb;
+    };
     static std::mutex mu;
-    static std::vector<std::pair<std::pair<const void*, int>, int>> cache;
+    static std::vector<Entry> cache;
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(mu);
     for (const auto& e : cache)
-        if (e.first.first == kernel && e.first.second == dev) return e.second;
+        if (e.k == kernel && e.dev == dev && e.dyn == dyn_smem) return e.nb;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess || nb < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, dyn_smem) != cudaSuccess || nb < 1)
         nb = 1;
-    cache.push_back({{kernel, dev}, nb});
+    cache.push_back({kernel, dev, dyn_smem, nb});
     return nb;
 }
 

@@ -21,8 +21,9 @@ int sm_count();
 // Default persistent grid: blocks_per_sm resident blocks on every SM.
 int persistent_grid(const Tuning& t, int blocks_per_sm = 8);
 
-// Resident blocks per SM of a kernel at kBlock threads (cached per kernel).
-int occupancy_of(const void* kernel, int threads);
+// Resident blocks per SM of a kernel at `threads` threads and `dyn_smem`
+// bytes of dynamic shared memory (cached).
+int occupancy_of(const void* kernel, int threads, size_t dyn_smem = 0);
 
 // Grid of a persistent (grid-stride) kernel: every block resident at once,
 // unless the tuning fixes the grid size.

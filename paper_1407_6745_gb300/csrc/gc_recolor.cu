@@ -95,6 +95,7 @@ struct RcArgs {
     const int64_t* cls_base;
     int32_t ngraphs;
     int32_t fuse_hist;    // 1: the recoloring kernel fills nxt_cnt (one graph only)
+    int32_t hist_smem;    // entries of its dynamic shared-memory histogram (0: global)
     int32_t* gpresent;    // per (graph, color): present colors, sizes, order, shuffle
     int32_t* gpsize;
     int32_t* gorder;
@@ -499,9 +500,13 @@ struct RecolorFetch {
     }
 };
 
-// Histogram of the new colors for the next iteration: shared-memory counts
-// when they fit, flushed once per block.
-constexpr int kRcHistSmem = 2048;
+// Histogram of the new colors for the next iteration: counts in dynamic
+// shared memory sized to the colors (up to 1023 colors), flushed once per
+// block; beyond that, global counts, where the lanes of a warp that add to
+// the same (color, bucket) are merged into one atomic (most vertices of a
+// skewed graph take the same few colors, and unmerged adds to one global
+// counter serialise in L2).
+constexpr int kRcHistSmem = 6144;
 
 struct NextHist {
     int32_t* sh;     // nullptr: count in global memory
@@ -511,8 +516,13 @@ struct NextHist {
     __device__ __forceinline__ void add(int32_t c, int b, int32_t chunks) const {
         if (c < 1 || c > cap) return;
         const int32_t key = c * kNB + b;
-        if (sh) atomicAdd(&sh[key], 1);
-        else atomicAdd(&glob[key], 1);
+        if (sh) {
+            atomicAdd(&sh[key], 1);
+        } else {
+            const unsigned act = __activemask();
+            const unsigned peers = __match_any_sync(act, key);
+            if (lane_id() == __ffs(peers) - 1) atomicAdd(&glob[key], __popc(peers));
+        }
         if (b == 0) atomicAdd(&units[c], chunks);
     }
 };
@@ -626,10 +636,9 @@ constexpr int kSegSmem = 1024;
 // that tile: the waits always end.
 __device__ __forceinline__ NextHist setup_next_hist(const RcArgs& a, int32_t* s_hist) {
     if (!a.fuse_hist) return NextHist{nullptr, nullptr, nullptr, 0};  // cap 0: add() is a no-op
-    const int32_t entries = (a.cap + 1) * kNB;
-    const bool local = entries <= kRcHistSmem;
+    const bool local = a.hist_smem > 0;  // (cap + 1) * kNB entries of dynamic shared memory
     if (local)
-        for (int i = threadIdx.x; i < entries; i += kBlock) s_hist[i] = 0;
+        for (int i = threadIdx.x; i < a.hist_smem; i += kBlock) s_hist[i] = 0;
     return NextHist{local ? s_hist : nullptr, a.nxt_cnt, a.nxt_units, a.cap};
 }
 
@@ -644,7 +653,7 @@ __device__ __forceinline__ void flush_next_hist(const RcArgs& a, const NextHist&
 __global__ void __launch_bounds__(kBlock, 5) k_rc_recolor_coop(RcArgs a) {
     __shared__ uint32_t s_bm[kWarps][kWarpBitmapWords];
     __shared__ int32_t s_tp[kSegSmem + 1], s_ss[kSegSmem + 1];
-    __shared__ int32_t s_hist[kRcHistSmem];
+    extern __shared__ int32_t s_hist[];
     if (a.ctrl->err & (kErrImproper | kErrBadGraph)) return;
     const int32_t total = a.ctrl->total_tiles;
     const int32_t nseg = a.ctrl->k * kNB;
@@ -677,7 +686,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_rc_recolor_coop(RcArgs a) {
 __global__ void __launch_bounds__(kBlock, 5) k_rc_recolor_step(RcArgs a, int32_t p, int32_t t0,
                                                                int32_t t1) {
     __shared__ uint32_t s_bm[kWarps][kWarpBitmapWords];
-    __shared__ int32_t s_hist[kRcHistSmem];
+    extern __shared__ int32_t s_hist[];
     if (a.ctrl->err & (kErrImproper | kErrBadGraph)) return;
     const NextHist nh = setup_next_hist(a, s_hist);
     __syncthreads();
@@ -884,9 +893,6 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
     const Tuning tune = current_tuning();
     const int grid = persistent_grid(tune);
     const int vgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, grid)));
-    const int coop_capacity = sm_count() * occupancy_of(reinterpret_cast<const void*>(k_rc_recolor_coop), kBlock);
-    const int grid_rc = std::min(resident_grid(k_rc_recolor_coop, tune), coop_capacity);
-    const int grid_step = resident_grid(k_rc_recolor_step, tune);
     const int grid_sc = static_cast<int>(std::max<int64_t>(
         1, std::min<int64_t>((n + kBlock - 1) / kBlock, resident_grid(k_rc_scatter, tune))));
     cudaError_t ce;
@@ -966,6 +972,15 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
     a.hub_bm = sc_hb.as<uint32_t>();
     a.hub_words = hub_words;
     a.fuse_hist = 1;
+    const int32_t hist_entries = static_cast<int32_t>(ent);
+    const size_t hist_dyn = hist_entries <= kRcHistSmem ? static_cast<size_t>(hist_entries) * 4 : 0;
+    a.hist_smem = hist_dyn ? hist_entries : 0;
+    const int coop_capacity =
+        sm_count() * occupancy_of(reinterpret_cast<const void*>(k_rc_recolor_coop), kBlock, hist_dyn);
+    const int grid_rc = tune.grid_blocks > 0 ? std::min(tune.grid_blocks, coop_capacity) : coop_capacity;
+    const int step_capacity =
+        sm_count() * occupancy_of(reinterpret_cast<const void*>(k_rc_recolor_step), kBlock, hist_dyn);
+    const int grid_step = tune.grid_blocks > 0 ? tune.grid_blocks : step_capacity;
     cudaMemsetAsync(a.ncolors, 0, (iterations + 1) * 4, s);
 
     cudaEvent_t e0, e1;
@@ -1001,7 +1016,7 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
             cudaError_t le;
             GC_LAUNCH(KID_RC_RECOLOR, s,
                       le = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_rc_recolor_coop),
-                                                       dim3(grid_rc), dim3(kBlock), args, 0, s));
+                                                       dim3(grid_rc), dim3(kBlock), args, hist_dyn, s));
             if (le != cudaSuccess) { st = cuda_status(le); break; }
         } else {
             RcCtrl hc;
@@ -1016,7 +1031,7 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
                 const int32_t t0 = tp[p * kNB], t1 = tp[(p + 1) * kNB];
                 if (t1 <= t0) continue;
                 const int g2 = std::min(grid_step, (t1 - t0 + kWarps - 1) / kWarps);
-                GC_LAUNCH(KID_RC_STEP, s, k_rc_recolor_step<<<g2, kBlock, 0, s>>>(a, p, t0, t1));
+                GC_LAUNCH(KID_RC_STEP, s, k_rc_recolor_step<<<g2, kBlock, hist_dyn, s>>>(a, p, t0, t1));
             }
         }
         cur = dst;
