@@ -104,10 +104,20 @@ def _peak_hbm():
         return 6800.0, "fallback"
 
 
-def _source_hash():
+# The sources each profiled kernel is compiled from: a committed DRAM-traffic
+# figure stays valid while these files are unchanged.
+KERNEL_SOURCES = {
+    "k_rc_recolor_coop": ["gc_recolor.cu", "gc_common.cuh", "gc_internal.h"],
+    "k_rc_recolor_step": ["gc_recolor.cu", "gc_common.cuh", "gc_internal.h"],
+    "spec_rounds_graph": ["gc_color.cu", "gc_common.cuh", "gc_internal.h"],
+}
+
+
+def _source_hash(kernel=None):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1407_6745_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    names = KERNEL_SOURCES.get(kernel) or sorted(os.listdir(csrc))
+    for name in sorted(names):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -119,7 +129,7 @@ def _traffic(kernel: str, workload: str):
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    src = _source_hash()
+    src = _source_hash(kernel)
     with open(p) as f:
         for line in f:
             if line.startswith("#") or "=" not in line:
