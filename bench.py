@@ -264,6 +264,71 @@ def run_reference(args, wl, g):
     print(json.dumps(line), flush=True)
 
 
+def _init_ranks():
+    """(world size, rank, local rank, device) for one process per GPU; NCCL
+    process group when launched by torchrun with more than one rank."""
+    ws, rank, local = _dist()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if ws > 1 and not torch.distributed.is_initialized():
+        torch.distributed.init_process_group("nccl", device_id=dev)
+    return ws, rank, local, dev
+
+
+def _barrier():
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.barrier()
+
+
+def run_reference_graphs(args):
+    """The reference arm of the many-graph workloads: the CPU oracle coloring
+    and recoloring the workload's graphs one after the other, on a bounded
+    sample (the first graphs of the workload, about 10 s per step); rank 0 only."""
+    import oracle
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    if args.workload == "batch":
+        plan = gg.batch_mix_plan(args.batch_count, 6, 1e3, args.batch_nmax)
+        jobs = [(i, dict(X=4, seed=1000 + i, perm="RV", iterations=5, perm_seed=0)) for i in range(len(plan))]
+        build = lambda i: gg.build_planned(plan[i])
+    else:
+        pool = serve_pool(args.serve_pool, 7, "cuda" if torch.cuda.is_available() else "cpu")
+        reqs = serve_requests(pool, args.serve_requests, 7)
+        jobs = [(r["graph"], dict(X=1, seed=r["seed"], perm=r["perm"], iterations=r["iterations"],
+                                  perm_seed=r["perm_seed"])) for r in reqs]
+        build = lambda i: gg.CSRGraph(pool[i][1], pool[i][2], pool[i][0])
+
+    def step(budget_s):
+        done, t0 = 0, time.perf_counter()
+        for i, p in jobs:
+            off, idx = build(i).numpy()
+            c, _ = oracle.color(off, idx, p["X"], p["seed"])
+            oracle.recolor(off, idx, c, p["perm"], p["iterations"], p["perm_seed"])
+            done += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        return done, time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        step(1.0)
+    done, sec = 0, 0.0
+    for _ in range(args.steps):
+        d, t = step(10.0)
+        done += d
+        sec += t
+    value = done / sec
+    sample = f"the first {done // max(args.steps, 1)} graphs of the workload per step, one at a time"
+    line = {"impl": "reference", "metric": "batched graphs/s vs one-by-one" if args.workload == "batch"
+            else "served graphs/s (e2e, saturated) vs one-by-one", "value": value, "unit": "graphs/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args):
     """Batched workload: `batch_count` graphs (half G(n, p) with mean degree
     U[8, 32], half 2D 5-point / 3D 7-point grids, n log-uniform in
@@ -271,20 +336,24 @@ def run_batch(args):
     iterations; knobs autotuned on the batch.  Batched = one
     gc_color_recolor_batch over the concatenated CSR; one-by-one = a
     gc_color_recolor call per graph on the same GPU.  Colors are compared
-    graph by graph (bit-exact)."""
+    graph by graph (bit-exact).  With N ranks the graphs are packed onto the
+    ranks by their expected entries (no exchange between ranks); every graph
+    keeps its global index for its seeds, so its colors do not depend on N."""
     import paper_1407_6745_gb300 as gc
-    from paper_1407_6745_gb300 import autotune
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    from paper_1407_6745_gb300 import autotune, shard
+    ws, rank, local, dev = _init_ranks()
     gc.load()
     t0 = time.perf_counter()
-    graphs = gg.batch_mix(args.batch_count, 6, 1e3, args.batch_nmax, device=dev)
+    plan = gg.batch_mix_plan(args.batch_count, 6, 1e3, args.batch_nmax)
+    parts = shard.partition([p[4] for p in plan], ws)
+    mine = parts[rank]
+    graphs = gg.batch_mix(args.batch_count, 6, 1e3, args.batch_nmax, device=dev, only=mine)
     union = gg.batch_union(graphs, device=dev)
     torch.cuda.synchronize(dev)
     torch.cuda.empty_cache()  # generation temporaries back to the device
     gen_s = time.perf_counter() - t0
     desc = [dict(n=g.n, seed=1000 + i, X=4, perm="RV", iterations=5, perm_seed=0)
-            for i, g in enumerate(graphs)]
+            for i, g in zip(mine, graphs)]
     total_nnz = union.nnz
     knobs, tuned_ms = autotune.autotune(union.offsets, union.idx, "RXF", 4, 1000, "RV", 5, repeats=1)
     gc.gc_set_tuning(**knobs)
@@ -293,26 +362,32 @@ def run_batch(args):
         gc.gc_color_recolor_batch(union.offsets, union.idx, desc, out=out)
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = gc.gc_kernel_launches()
+    _barrier()
     torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for _ in range(args.steps):
-        _, rounds, maxc, _ = gc.gc_color_recolor_batch(union.offsets, union.idx, desc, out=out)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    batch_ms = e0.elapsed_time(e1) / args.steps
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, rounds, maxc, _ = gc.gc_color_recolor_batch(union.offsets, union.idx, desc, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    _barrier()
+    launches = gc.gc_kernel_launches() - launches0
+    batch_ms = shard.max_over_ranks(e0.elapsed_time(e1) / args.steps)
     # one graph at a time
     outs = [torch.empty(g.n, dtype=torch.int32, device=dev) for g in graphs]
     for g, d, o in zip(graphs, desc, outs):
         gc.gc_color_recolor(g.offsets, g.idx, "RXF", 4, d["seed"], "RV", 5, 0, out=o)
+    _barrier()
     torch.cuda.synchronize(dev)
     e0.record(stream)
     for g, d, o in zip(graphs, desc, outs):
         gc.gc_color_recolor(g.offsets, g.idx, "RXF", 4, d["seed"], "RV", 5, 0, out=o)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    single_ms = e0.elapsed_time(e1)
-    identical = bool(torch.equal(torch.cat(outs), out))
-    # the oracle on the smallest graphs
+    single_ms = shard.max_over_ranks(e0.elapsed_time(e1))
+    identical = bool(torch.equal(torch.cat(outs), out)) if outs else True
+    # the oracle on the smallest graphs of this rank
     import oracle
     small = sorted(range(len(graphs)), key=lambda i: graphs[i].n)[:4]
     oracle_ok = True
@@ -323,20 +398,35 @@ def run_batch(args):
         orc, _ = oracle.recolor(off, idx, oc, "RV", 5, 0)
         oracle_ok &= bool(np.array_equal(out[base[i]:base[i + 1]].cpu().numpy(), orc))
     gc.gc_set_tuning()
-    line = {"metric": "batched graphs/s vs one-by-one", "value": len(graphs) / (batch_ms * 1e-3),
-            "unit": "graphs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+    rows = shard.gather(dict(n=union.n, nnz=total_nnz, graphs=len(graphs), identical=identical,
+                             oracle_ok=oracle_ok, maxc=[int(x) for x in maxc], rounds=[int(x) for x in rounds],
+                             knobs=knobs, clocks=clk.summary(), launches=launches, gen_s=gen_s))
+    if rank != 0:
+        return
+    total_graphs = sum(r["graphs"] for r in rows)
+    tot_n = sum(r["n"] for r in rows)
+    tot_nnz = sum(r["nnz"] for r in rows)
+    allmaxc = [m for r in rows for m in r["maxc"]]
+    line = {"metric": "batched graphs/s vs one-by-one", "value": total_graphs / (batch_ms * 1e-3),
+            "unit": "graphs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"batch of {len(graphs)} graphs: half G(n,p) mean degree U[8,32], "
+            "config": {"workload": f"batch of {total_graphs} graphs: half G(n,p) mean degree U[8,32], "
                                    f"half 2D 5-pt / 3D 7-pt grids, n log-uniform [1e3, {args.batch_nmax:g}], "
-                                   "Random-4 Fit + 5 RV iterations each", "graphs": len(graphs),
-                       "total_n": union.n, "total_nnz": total_nnz, "knobs": knobs,
-                       "generation_s": round(gen_s, 1)},
-            "one_by_one": {"graphs_per_s": len(graphs) / (single_ms * 1e-3), "ms": single_ms},
+                                   "Random-4 Fit + 5 RV iterations each", "graphs": total_graphs,
+                       "total_n": tot_n, "total_nnz": tot_nnz, "knobs": rows[0]["knobs"],
+                       "generation_s": round(max(r["gen_s"] for r in rows), 1),
+                       "parallelism": (f"graphs packed on {ws} GPUs by expected entries, no exchange"
+                                       if ws > 1 else "single GPU"),
+                       "l2": "inputs larger than L2" if 4 * tot_nnz > L2_BYTES else "inputs smaller than L2"},
+            "one_by_one": {"graphs_per_s": total_graphs / (single_ms * 1e-3), "ms": single_ms},
             "speedup_vs_one_by_one": single_ms / batch_ms,
-            "gteps_batched": total_nnz * 6 / (batch_ms * 1e-3) / 1e9,
-            "parity": {"batched_equals_one_by_one": identical, "oracle_on_4_smallest": oracle_ok},
-            "colors": {"max_after_recoloring_mean": float(np.mean(maxc)), "rounds_max": max(rounds)}}
+            "gteps_batched": tot_nnz * 6 / (batch_ms * 1e-3) / 1e9,
+            "parity": {"batched_equals_one_by_one": all(r["identical"] for r in rows),
+                       "oracle_on_4_smallest_per_rank": all(r["oracle_ok"] for r in rows)},
+            "colors": {"max_after_recoloring_mean": float(np.mean(allmaxc)) if allmaxc else 0.0,
+                       "rounds_max": max((m for r in rows for m in r["rounds"]), default=0)},
+            "clocks": rows[0]["clocks"], "gpu_launches": sum(r["launches"] for r in rows)}
     print(json.dumps(line), flush=True)
 
 
@@ -386,18 +476,24 @@ def run_serve(args):
     one-by-one = a gc_color_recolor call per request from the same pinned host
     buffers; then Poisson arrivals (seed 7) at `serve_load` x capacity, with
     p50/p99 submit-to-result latency.  All three run end to end: graphs in
-    pinned host memory, colors back in host memory."""
+    pinned host memory, colors back in host memory.  With N ranks the
+    requests are packed onto the ranks by their entries, each rank serving its
+    share (arriving at their times in the one Poisson stream); the job time is
+    the slowest rank's and the latencies are pooled on rank 0."""
     import threading
     import paper_1407_6745_gb300 as gc
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    from paper_1407_6745_gb300 import shard
+    ws, rank, local, dev = _init_ranks()
     gc.load()
     t0 = time.perf_counter()
     pool = serve_pool(args.serve_pool, 7, dev)
     torch.cuda.synchronize(dev)
     torch.cuda.empty_cache()
     gen_s = time.perf_counter() - t0
-    reqs = serve_requests(pool, args.serve_requests, 7)
+    all_reqs = serve_requests(pool, args.serve_requests, 7)
+    parts = shard.partition([pool[r["graph"]][2].numel() for r in all_reqs], ws)
+    mine = parts[rank]
+    reqs = [all_reqs[i] for i in mine]
     free, _ = torch.cuda.mem_get_info(dev)
     budget = int(free * 0.6)
 
@@ -408,22 +504,27 @@ def run_serve(args):
 
     def burst(reqs_, max_batch, workers):
         with gc.gc_server_create(budget, max_batch, workers) as srv:
+            t = time.perf_counter()
             ts = [submit(srv, r) for r in reqs_]
-            res = [gc.gc_server_wait(srv, t) for t in ts]
+            res = [gc.gc_server_wait(srv, t_) for t_ in ts]
+            span = time.perf_counter() - t
             info = gc.gc_server_stats(srv)
-        return res, info
+        return res, info, span
 
     # warm-up: every graph of the pool once, through the server
     burst([dict(graph=i, seed=1, iterations=1, perm="RV", perm_seed=0) for i in range(len(pool))],
           args.serve_batch, args.serve_workers)
     launches0 = gc.gc_kernel_launches()
-    with Clocks(0) as clk:
-        res, info = burst(reqs, args.serve_batch, args.serve_workers)
-    capacity = info["graphs_per_s"]
+    _barrier()
+    with Clocks(local) as clk:
+        res, info, span = burst(reqs, args.serve_batch, args.serve_workers)
     launches = gc.gc_kernel_launches() - launches0
+    span = shard.max_over_ranks(span)
+    capacity = len(all_reqs) / span
 
     # one graph at a time, same host buffers
     outs = {}
+    _barrier()
     torch.cuda.synchronize(dev)
     t1 = time.perf_counter()
     for i, r in enumerate(reqs):
@@ -432,15 +533,17 @@ def run_serve(args):
                                              r["perm_seed"])
         if i < args.serve_check:
             outs[i] = (col, nc[-1], st["rounds"])
-    single_s = time.perf_counter() - t1
-    single_gps = len(reqs) / single_s
+    single_s = shard.max_over_ranks(time.perf_counter() - t1)
+    single_gps = len(all_reqs) / single_s
     parity = all(torch.equal(res[i][0], outs[i][0]) and res[i][1]["max_color"] == outs[i][1]
                  and res[i][1]["rounds"] == outs[i][2] for i in outs)
 
-    # Poisson arrivals at serve_load x capacity
+    # Poisson arrivals at serve_load x capacity; this rank's requests arrive
+    # at their times in the one stream
     rate = args.serve_load * capacity
-    gaps = np.random.default_rng(7).exponential(1.0 / rate, size=len(reqs))
-    arrivals = np.cumsum(gaps)
+    arrivals_all = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, size=len(all_reqs)))
+    arrivals = arrivals_all[mine] if len(mine) else arrivals_all[:0]
+    _barrier()
     with gc.gc_server_create(budget, args.serve_batch, args.serve_workers) as srv:
         tickets = [None] * len(reqs)
 
@@ -458,9 +561,10 @@ def run_serve(args):
         pres = [gc.gc_server_wait(srv, t) for t in tickets]
         pinfo = gc.gc_server_stats(srv)
     ppar = all(torch.equal(pres[i][0], res[i][0]) for i in range(len(reqs)))
+    lat = [p[1]["done_ms"] - p[1]["submit_ms"] for p in pres]
     batch_sizes = [p[1]["batch_size"] for p in pres]
 
-    # the oracle on the two smallest requests
+    # the oracle on this rank's two smallest requests
     import oracle
     small = sorted(range(len(reqs)), key=lambda i: pool[reqs[i]["graph"]][1].numel())[:2]
     oracle_ok = True
@@ -470,40 +574,54 @@ def run_serve(args):
         oc, _ = oracle.color(off.numpy(), idx.numpy(), 1, r["seed"])
         orc, _ = oracle.recolor(off.numpy(), idx.numpy(), oc, r["perm"], r["iterations"], r["perm_seed"])
         oracle_ok &= bool(np.array_equal(res[i][0].numpy(), orc))
-
-    n_tot = sum(pool[r["graph"]][1].numel() - 1 for r in reqs)
-    nnz_tot = sum(pool[r["graph"]][2].numel() for r in reqs)
-    passes = sum(pool[r["graph"]][2].numel() * (1 + r["iterations"]) for r in reqs)
+    rows = shard.gather(dict(lat=lat, batch_sizes=batch_sizes, parity=parity, ppar=ppar, oracle_ok=oracle_ok,
+                             sat_p50=info["p50_ms"], sat_p99=info["p99_ms"], batches=info["batches"],
+                             pbatches=pinfo["batches"], peak=pinfo["bytes_peak"], clocks=clk.summary(),
+                             launches=launches, checked=len(outs), last_done=pinfo["graphs_per_s"]))
+    if rank != 0:
+        return
+    lat_all = np.array([x for r in rows for x in r["lat"]])
+    bs_all = [x for r in rows for x in r["batch_sizes"]]
+    n_tot = sum(pool[r["graph"]][1].numel() - 1 for r in all_reqs)
+    nnz_tot = sum(pool[r["graph"]][2].numel() for r in all_reqs)
+    passes = sum(pool[r["graph"]][2].numel() * (1 + r["iterations"]) for r in all_reqs)
+    p50, p99 = (float(np.percentile(lat_all, 50)), float(np.percentile(lat_all, 99))) if len(lat_all) else (0.0, 0.0)
     line = {"metric": "served graphs/s (e2e, saturated) vs one-by-one; p50/p99 latency at "
                       f"{args.serve_load:g} x capacity",
-            "value": capacity, "unit": "graphs/s", "n_gpus": 1, "steps": 1, "warmup": 1,
-            "ms_per_step": 1e3 * len(reqs) / capacity, "higher_is_better": True, "scaling": "weak",
+            "value": capacity, "unit": "graphs/s", "n_gpus": ws, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * span, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"{len(reqs)} requests over a pool of {len(pool)} graphs: G(n,p) n "
+            "config": {"workload": f"{len(all_reqs)} requests over a pool of {len(pool)} graphs: G(n,p) n "
                                    "log-uniform [1e3,1e6] mean degree U[8,32] / 27-pt stencil side "
                                    "U[16,128] / R-MAT scale U[14,22] ef 16, uniform; First Fit + "
                                    "k~U[1,20] recoloring iterations, perm uniform {RV,NI,RAND}; seed 7",
-                       "requests": len(reqs), "pool": len(pool), "total_n": n_tot, "total_nnz": nnz_tot,
+                       "requests": len(all_reqs), "pool": len(pool), "total_n": n_tot, "total_nnz": nnz_tot,
                        "edge_passes": passes, "max_batch": args.serve_batch,
                        "workers": args.serve_workers, "mem_budget_bytes": budget,
                        "generation_s": round(gen_s, 1),
+                       "parallelism": (f"requests packed on {ws} GPUs by entries, no exchange"
+                                       if ws > 1 else "single GPU"),
                        "l2": "graphs from pinned host memory; most inputs larger than L2"},
-            "saturated": {"graphs_per_s": capacity, "gteps": passes / (len(reqs) / capacity) / 1e9,
-                          "p50_ms": info["p50_ms"], "p99_ms": info["p99_ms"], "batches": info["batches"]},
+            "saturated": {"graphs_per_s": capacity, "gteps": passes / span / 1e9,
+                          "p50_ms_rank0": rows[0]["sat_p50"], "p99_ms_rank0": rows[0]["sat_p99"],
+                          "batches": sum(r["batches"] for r in rows)},
             "one_by_one": {"graphs_per_s": single_gps, "s": single_s},
             "speedup_vs_one_by_one": capacity / single_gps,
-            "poisson": {"rate_graphs_per_s": rate, "load": args.serve_load,
-                        "graphs_per_s": pinfo["graphs_per_s"], "p50_ms": pinfo["p50_ms"],
-                        "p99_ms": pinfo["p99_ms"], "mean_ms": pinfo["mean_ms"],
-                        "batches": pinfo["batches"], "mean_batch": float(np.mean(batch_sizes)),
-                        "max_batch_seen": int(max(batch_sizes)), "peak_bytes": pinfo["bytes_peak"]},
-            "parity": {f"served_equals_alone_first_{len(outs)}": parity,
-                       "poisson_equals_saturated_all": ppar, "oracle_on_2_smallest": oracle_ok},
+            "poisson": {"rate_graphs_per_s": rate, "load": args.serve_load, "p50_ms": p50, "p99_ms": p99,
+                        "mean_ms": float(lat_all.mean()) if len(lat_all) else 0.0,
+                        "batches": sum(r["pbatches"] for r in rows),
+                        "mean_batch": float(np.mean(bs_all)) if bs_all else 0.0,
+                        "max_batch_seen": int(max(bs_all)) if bs_all else 0,
+                        "peak_bytes_rank0": rows[0]["peak"]},
+            "parity": {"served_equals_alone_checked": sum(r["checked"] for r in rows),
+                       "served_equals_alone": all(r["parity"] for r in rows),
+                       "poisson_equals_saturated_all": all(r["ppar"] for r in rows),
+                       "oracle_on_2_smallest_per_rank": all(r["oracle_ok"] for r in rows)},
             "e2e": {"value": capacity, "unit": "graphs/s",
                     "h2d_bytes_per_step": int(sum(8 * (pool[r["graph"]][1].numel()) + 4 * pool[r["graph"]][2].numel()
-                                                  for r in reqs)),
+                                                  for r in all_reqs)),
                     "d2h_bytes_per_step": int(4 * n_tot)},
-            "clocks": clk.summary(), "gpu_launches": launches}
+            "clocks": rows[0]["clocks"], "gpu_launches": sum(r["launches"] for r in rows)}
     print(json.dumps(line), flush=True)
 
 
@@ -525,11 +643,13 @@ def main():
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-check", type=int, default=40)
     args = ap.parse_args()
-    if args.workload == "batch":
-        run_batch(args)
+    if args.workload in ("batch", "serve") and args.impl == "reference":
+        run_reference_graphs(args)
         return
-    if args.workload == "serve":
-        run_serve(args)
+    if args.workload in ("batch", "serve"):
+        (run_batch if args.workload == "batch" else run_serve)(args)
+        if torch.distributed.is_available() and torch.distributed.is_initialized():
+            torch.distributed.destroy_process_group()
         return
     wl = WORKLOADS[args.workload]
     ws, rank, local = _dist()

@@ -307,24 +307,45 @@ def batch_union(graphs, device=None) -> CSRGraph:
                     f"batch{len(graphs)}")
 
 
-def batch_mix(count: int, seed: int, n_lo: float, n_hi: float, device="cpu"):
-    """The batch workload: `count` graphs, half G(n, p) with mean degree drawn
-    from U[8, 32], half 2D 5-point or 3D 7-point grids; n log-uniform in
-    [n_lo, n_hi].  Returns the graphs (each with its own ids)."""
+def batch_mix_plan(count: int, seed: int, n_lo: float, n_hi: float):
+    """The graphs of batch_mix as specifications, with their expected
+    adjacency entries (to place them before building them): a list of
+    (kind, size parameter, mean degree or None, generator seed, est. entries)."""
     rng = np.random.default_rng(seed)
-    out = []
+    plan = []
     for i in range(count):
         n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
         if i % 2 == 0:
-            out.append(erdos_renyi(max(n, 2), float(rng.uniform(8.0, 32.0)), seed=seed * 100003 + i,
-                                   device=device))
+            n = max(n, 2)
+            d = float(rng.uniform(8.0, 32.0))
+            plan.append(("er", n, d, seed * 100003 + i, int(n * d)))
         elif rng.random() < 0.5:
             side = max(2, int(round(math.sqrt(n))))
-            out.append(grid_2d(side, side, device=device))
+            plan.append(("grid2d", side, None, 0, 4 * side * side))
         else:
             side = max(2, int(round(n ** (1.0 / 3.0))))
-            out.append(stencil_3d(side, side, side, points=7, device=device))
-    return out
+            plan.append(("st7", side, None, 0, 6 * side ** 3))
+    return plan
+
+
+def build_planned(spec, device="cpu") -> CSRGraph:
+    kind, size, d, gseed, _ = spec
+    if kind == "er":
+        return erdos_renyi(size, d, seed=gseed, device=device)
+    if kind == "grid2d":
+        return grid_2d(size, size, device=device)
+    return stencil_3d(size, size, size, points=7, device=device)
+
+
+def batch_mix(count: int, seed: int, n_lo: float, n_hi: float, device="cpu", only=None):
+    """The batch workload: `count` graphs, half G(n, p) with mean degree drawn
+    from U[8, 32], half 2D 5-point or 3D 7-point grids; n log-uniform in
+    [n_lo, n_hi].  Returns the graphs (each with its own ids); with `only`,
+    just the graphs of those indices (in that order), the same as in the
+    full list."""
+    plan = batch_mix_plan(count, seed, n_lo, n_hi)
+    pick = range(count) if only is None else only
+    return [build_planned(plan[i], device) for i in pick]
 
 
 # ---------------------------------------------------------------------------
