@@ -171,6 +171,19 @@ static int check_graph(int64_t n, const int64_t* off, const int32_t* idx)
     return OR_OK;
 }
 
+/* The graph to be colored must have no self-loop: C(u) != C(v) cannot hold on
+ * an edge (v, v) (Sec. 1).  (Validation instead counts a loop as a conflict.) */
+static int check_colorable(int64_t n, const int64_t* off, const int32_t* idx)
+{
+    int64_t v, e;
+    int status = check_graph(n, off, idx);
+    if (status != OR_OK) return status;
+    for (v = 0; v < n; ++v)
+        for (e = off[v]; e < off[v + 1]; ++e)
+            if ((int64_t)idx[e] == v) return OR_ERR_BAD_GRAPH;
+    return OR_OK;
+}
+
 static int64_t max_degree(int64_t n, const int64_t* off)
 {
     int64_t v, d = 0;
@@ -237,7 +250,7 @@ static int color_core(int64_t n, const int64_t* off, const int32_t* idx,
 
     memset(&local, 0, sizeof(local));
     if (X < 1) return OR_ERR_INVALID_ARG;
-    status = check_graph(n, off, idx);
+    status = check_colorable(n, off, idx);
     if (status != OR_OK) return status;
     if (n == 0) { if (st) *st = local; return OR_OK; }
 
@@ -591,7 +604,7 @@ int oracle_color_lf(int64_t n, const int64_t* off, const int32_t* idx, int32_t X
     int64_t v;
     int status;
     if (n > 0 && !colors_out) return OR_ERR_INVALID_ARG;
-    status = check_graph(n, off, idx);
+    status = check_colorable(n, off, idx);
     if (status != OR_OK) return status;
     prio = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
     if (!prio) return OR_ERR_OOM;
@@ -689,7 +702,7 @@ int oracle_greedy_sequential(int64_t n, const int64_t* off, const int32_t* idx, 
     int64_t v, e, i, maxd, d;
     int status;
     if (order_kind != 0 && order_kind != 1) return OR_ERR_INVALID_ARG;
-    status = check_graph(n, off, idx);
+    status = check_colorable(n, off, idx);
     if (status != OR_OK) return status;
     if (n == 0) return OR_OK;
     maxd = max_degree(n, off);

@@ -572,6 +572,23 @@ def test_rxf_draw_index_mapping():
 # Error behaviour
 # --------------------------------------------------------------------------
 
+def test_self_loop_is_a_malformed_graph():
+    """C(u) != C(v) on every edge cannot hold on a loop (Sec. 1)."""
+    g = gg.path(4)
+    off, idx = _np(g)
+    idx = idx.copy()
+    idx[0] = 0  # row 0 lists itself
+    for call in (lambda: oracle.color(off, idx, 1, 0), lambda: oracle.color_lf(off, idx, 1, 0),
+                 lambda: oracle.greedy_sequential(off, idx, "NAT")):
+        with pytest.raises(oracle.OracleError) as e:
+            call()
+        assert e.value.code == oracle.ERR_BAD_GRAPH
+    # as a coloring to recolor it is improper: the loop is a conflict
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.recolor(off, idx, np.array([1, 2, 1, 2], dtype=np.int32), "RV", 1)
+    assert e.value.code == oracle.ERR_IMPROPER_INPUT
+
+
 def test_errors():
     off, idx = _np(gg.path(4))
     with pytest.raises(oracle.OracleError) as e:
