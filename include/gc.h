@@ -30,7 +30,10 @@
  *
  * Graph layout: symmetric CSR, offsets int64[n+1] with offsets[0] = 0,
  * non-decreasing, offsets[n] = nnz; idx int32[nnz] neighbor ids in [0, n).
- * Every undirected edge appears in both rows; duplicates are tolerated.
+ * Every undirected edge appears in both rows; duplicates are tolerated.  A
+ * self-loop makes a graph uncolorable: the coloring calls report it as
+ * GC_ERR_BAD_GRAPH, and a coloring given to gc_recolor / gc_validate counts
+ * it as a conflict.
  * Colors are int32, 1-based.
  *
  * Memory: every pointer argument of a call (graph arrays, colors in and out)

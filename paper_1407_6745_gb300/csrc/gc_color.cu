@@ -460,15 +460,16 @@ __device__ __forceinline__ bool loses(const SpecArgs& a, const WorkItem& it, int
     const unsigned long long* key = reinterpret_cast<const unsigned long long*>(a.key);
     const uint64_t kv = __ldg(key + it.v);
     const uint32_t tv = static_cast<uint32_t>(kv >> 32);
-    bool lose = false;
+    bool lose = false, loop = false;
     for_each_nbr<UC, uint64_t, true>(
         a.g, it.beg, it.deg, lane0, stride, [&](int32_t u) { return __ldg(key + u); },
         [&](int32_t u, uint64_t ku) {
-            if (u != it.v && static_cast<uint32_t>(ku >> 32) == tv &&
-                (ku > kv || (ku == kv && u > it.v)))
+            if (u == it.v) loop = true;  // uncolorable (Sec. 1): reported as a malformed graph
+            else if (static_cast<uint32_t>(ku >> 32) == tv && (ku > kv || (ku == kv && u > it.v)))
                 lose = true;
         },
         &a.ctrl->err);
+    if (loop) atomicOr(&a.ctrl->err, kErrBadGraph);
     return lose;
 }
 
