@@ -368,7 +368,9 @@ gc_status gc_check_graph(const gc_graph* g, int64_t* first_bad_vertex, void* str
  * setting).  A vertex of degree d with d + X <= 64 is handled by a group of
  * 4 lanes if d <= g4_max_deg, 8 if d <= g8_max_deg, 16 if d <= g16_max_deg,
  * else 32; otherwise by one warp with a shared-memory bitmap if
- * d <= warp_max_deg, else by a whole block.  grid_blocks = 0 sizes every
+ * d <= warp_max_deg, else by a whole block (coloring) or split into chunks
+ * of 256 neighbors (recoloring, where rc_warp_max_deg takes the place of
+ * warp_max_deg).  grid_blocks = 0 sizes every
  * grid to the blocks that fit on the GPU at once.  recolor_mode 0 runs each recoloring iteration as one dataflow
  * launch (vertices wait, with a bounded spin of spin_limit polls, for their
  * earlier-class neighbors); 1 launches one grid per color class.
@@ -387,6 +389,7 @@ typedef struct {
     int32_t recolor_mode;
     int32_t spin_limit;
     int32_t spec_graph;
+    int32_t rc_warp_max_deg;
 } gc_tuning;
 
 /* Sets the scheduling knobs (NULL restores the defaults).  GC_ERR_INVALID_ARG

@@ -46,7 +46,14 @@ struct Tuning {
     int32_t recolor_mode;  // 0 = dataflow (one launch), 1 = one launch per class
     int32_t spin_limit;    // bounded wait iterations in the dataflow recolor
     int32_t spec_graph;    // 1: speculative rounds in a CUDA graph WHILE node; 0: host loop
+    int32_t rc_warp_max_deg;  // warp_max_deg of the recoloring phase
 };
+
+// The recoloring phase's view of the knobs: its own warp threshold.
+__host__ __device__ inline Tuning recolor_tuning(Tuning t) {
+    t.warp_max_deg = t.rc_warp_max_deg;
+    return t;
+}
 
 __host__ __device__ inline int bucket_of(int64_t deg, int32_t X, const Tuning& t) {
     if (deg + (int64_t)X <= 64) {

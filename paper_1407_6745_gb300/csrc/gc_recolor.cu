@@ -24,7 +24,7 @@
 //                 waits.
 // The negative encoding makes one 4-byte gather per edge serve both "is u
 // earlier than v" and "what color did u take".  Rows longer than
-// warp_max_deg are cut into chunks of 512 neighbors handled by different
+// rc_warp_max_deg are cut into chunks of 256 neighbors handled by different
 // warps; the chunks OR their forbidden colors into a per-row bitmap and the
 // warp that finishes the last chunk picks the color.
 #include <algorithm>
@@ -38,7 +38,7 @@ namespace gc {
 constexpr int32_t kMaxInputColor = 1 << 28;
 constexpr int kOrderThreads = 1024;
 constexpr int kShuffleSmem = 4096;
-constexpr int32_t kChunk = 512;   // neighbors per chunk of a split (heavy) row
+constexpr int32_t kChunk = 256;   // neighbors per chunk of a split (heavy) row (measured best on R-MAT)
 
 // Vertices (or, bucket 0, row chunks) per warp tile.
 __host__ __device__ constexpr int warp_tile(int b) {
@@ -715,7 +715,7 @@ gc_status class_ranks_device(const Graph& g, const int32_t* colors, bool trusted
     const int64_t n = g.n;
     *maxc_out = 0;
     if (n == 0) return GC_OK;
-    const Tuning tune = current_tuning();
+    const Tuning tune = recolor_tuning(current_tuning());
     const int grid = persistent_grid(tune);
     const int vgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, grid)));
     Scratch sc_ctrl, sc_bucket;
@@ -890,7 +890,7 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
                          int32_t* ncolors_per_iter, gc_stats* stats, cudaStream_t s) {
     const int64_t n = g.n;
     if (stats) std::memset(stats, 0, sizeof(*stats));
-    const Tuning tune = current_tuning();
+    const Tuning tune = recolor_tuning(current_tuning());
     const int grid = persistent_grid(tune);
     const int vgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, grid)));
     const int grid_sc = static_cast<int>(std::max<int64_t>(
@@ -1072,7 +1072,7 @@ static gc_status recolor_batch_impl(const Graph& g, const gc_batch_graph* graphs
     if (stats) std::memset(stats, 0, sizeof(*stats));
     int32_t iters = 0;
     for (int32_t i = 0; i < ng; ++i) iters = std::max(iters, graphs[i].iterations);
-    const Tuning tune = current_tuning();
+    const Tuning tune = recolor_tuning(current_tuning());
     const int grid = persistent_grid(tune);
     const int vgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, grid)));
     const int coop_capacity = sm_count() * occupancy_of(reinterpret_cast<const void*>(k_rc_recolor_coop), kBlock);

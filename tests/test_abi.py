@@ -58,7 +58,7 @@ def test_argument_checks_need_no_gpu():
     with pytest.raises(gc.GCError):
         gc.gc_set_tuning(g4_max_deg=9, g8_max_deg=8)
     gc.gc_set_tuning()
-    assert gc.gc_get_tuning()["warp_max_deg"] == 512
+    assert gc.gc_get_tuning()["warp_max_deg"] == 1024 and gc.gc_get_tuning()["rc_warp_max_deg"] == 512
     for budget, max_batch, workers in ((0, 8, 2), (1 << 20, 0, 2), (1 << 20, 70000, 2), (1 << 20, 8, 0)):
         with pytest.raises(gc.GCError) as e:
             gc.gc_server_create(budget, max_batch, workers)

@@ -129,15 +129,17 @@ def test_presets(preset):
 # --------------------------------------------------------------------------
 
 THRESHOLD_DEGREES = [0, 1, 3, 4, 5, 7, 8, 9, 15, 16, 17, 31, 32, 33, 47, 48, 56, 57, 62, 63, 64,
-                     65, 100, 255, 256, 1023, 1024, 2047, 2048, 2049, 2050, 4000, 20000]
+                     65, 100, 255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 2047, 2048, 2049, 2050,
+                     4000, 20000]
 
 
 @pytest.mark.parametrize("strategy,X", [("FF", 1), ("RXF", 2), ("RXF", 8), ("RXF", 60),
                                         ("RXF", 3000)])
 def test_degree_thresholds(strategy, X):
     """Vertices exactly on every bucket boundary (4/8/16 lanes, deg + X = 64,
-    warp_max_deg = 2048) and Random-X draws beyond the 64-color register
-    window and the 2048-color warp bitmap."""
+    the warp thresholds of coloring (1024) and recoloring (512), the 256-entry
+    recoloring chunks) and Random-X draws beyond the 64-color register window
+    and the 2048-color warp bitmap."""
     g = gg.hubs(THRESHOLD_DEGREES, 30000, seed=3)
     c = _spec(g, strategy, X, 11)
     for perm in ("RV", "NI", "ND", "RAND"):
