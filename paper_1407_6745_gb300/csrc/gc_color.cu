@@ -321,6 +321,8 @@ __device__ __forceinline__ void tentative_group_tile(const SpecArgs& a, const Ro
 // below the one it was read from, after the whole chunk has been read), then
 // takes the j-th permissible color from the bitmap.  Past the bitmap's free
 // colors (Random-X with a large X) the row is scanned in full instead.
+constexpr int kHeavyU = 4;  // pending entries per thread per step of a heavy row
+
 __device__ int32_t choose_heavy(const SpecArgs& a, const WorkItem& it, uint32_t j, SpecShared& sm) {
     const int t = threadIdx.x, l = lane_id(), w = t >> 5;
     const HeavyRows hr = *a.heavy;
@@ -332,25 +334,44 @@ __device__ int32_t choose_heavy(const SpecArgs& a, const WorkItem& it, uint32_t 
     uint32_t* bm = hr.hbm + hr.h_bbeg[h];
     const int32_t words = hr.h_bwords[h];
     const uint32_t bits = 32u * static_cast<uint32_t>(words);
+    // this round's new forbidden colors gather in the block's shared bitmap
+    // (one block owns the row this round) and are merged once at the end;
+    // colors past it go to the global bitmap directly
+    const int32_t sw = min(words, kBlockBitmapWords);
+    const uint32_t sbits = 32u * static_cast<uint32_t>(sw);
+    for (int i = t; i < sw; i += kBlock) sm.blk.bm[i] = 0u;
+    __syncthreads();
     int32_t kept = 0;
-    for (int64_t i0 = 0; i0 < cnt; i0 += kBlock) {
-        const int64_t i = i0 + t;
-        int32_t u = 0;
-        bool keep = false;
-        if (i < cnt) {
-            u = src[i];
-            if (u < 0 || u >= a.g.n) {
-                atomicOr(&a.ctrl->err, kErrBadGraph);
-            } else {
-                const int32_t c = __ldg(a.color + u);
-                if (c == 0) keep = true;
-                else if (static_cast<uint32_t>(c - 1) < bits)
-                    atomicOr(bm + ((c - 1) >> 5), 1u << ((c - 1) & 31));
+    for (int64_t i0 = 0; i0 < cnt; i0 += static_cast<int64_t>(kHeavyU) * kBlock) {
+        int32_t u[kHeavyU], c[kHeavyU];
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k) {  // all loads of the step in flight together
+            const int64_t i = i0 + static_cast<int64_t>(k) * kBlock + t;
+            u[k] = i < cnt ? src[i] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k) {
+            const int64_t i = i0 + static_cast<int64_t>(k) * kBlock + t;
+            c[k] = -1;  // -1: no entry
+            if (i < cnt) {
+                if (u[k] < 0 || u[k] >= a.g.n) atomicOr(&a.ctrl->err, kErrBadGraph);
+                else c[k] = __ldg(a.color + u[k]);
             }
         }
-        const unsigned bal = __ballot_sync(kFull, keep);
-        if (l == 0) sm.blk.wsum[w] = static_cast<uint32_t>(__popc(bal));
-        __syncthreads();
+        int32_t mine = 0;
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k) {
+            if (c[k] == 0) {
+                ++mine;
+            } else if (c[k] > 0) {
+                const uint32_t b = static_cast<uint32_t>(c[k] - 1);
+                if (b < sbits) atomicOr(&sm.blk.bm[b >> 5], 1u << (b & 31));
+                else if (b < bits) atomicOr(bm + (b >> 5), 1u << (b & 31));
+            }
+        }
+        const int32_t incl_w = static_cast<int32_t>(warp_inclusive_scan(static_cast<uint32_t>(mine)));
+        if (l == 31) sm.blk.wsum[w] = static_cast<uint32_t>(incl_w);
+        __syncthreads();  // also: every read of this step is done before any write
         int32_t before = 0, total = 0;
 #pragma unroll
         for (int k = 0; k < kWarps; ++k) {
@@ -358,13 +379,21 @@ __device__ int32_t choose_heavy(const SpecArgs& a, const WorkItem& it, uint32_t 
             if (k < w) before += x;
             total += x;
         }
-        if (keep) dst[kept + before + __popc(bal & ((1u << l) - 1u))] = u;
+        int32_t pos = kept + before + incl_w - mine;  // at or below every position read this step
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k)
+            if (c[k] == 0) dst[pos++] = u[k];
         kept += total;
         __syncthreads();
     }
+    for (int i = t; i < sw; i += kBlock) {
+        const uint32_t x = sm.blk.bm[i];
+        if (x) bm[i] = __ldcg(bm + i) | x;  // the block owns these words this round
+    }
+    __syncthreads();
     if (t == 0) hr.h_pcnt[h] = kept;
     // the j-th free bit of the bitmap (bit b = color b + 1); L2 reads, since
-    // the block's own atomics went there
+    // the block's own writes went there
     for (int32_t w0 = 0; w0 < words; w0 += kBlock) {
         const int32_t wi = w0 + t;
         const uint32_t f = wi < words ? ~__ldcg(bm + wi) : 0u;
@@ -485,15 +514,32 @@ __device__ __forceinline__ bool loses_pending(const SpecArgs& a, const WorkItem&
     const uint64_t kv = __ldg(key + it.v);
     const uint32_t tv = static_cast<uint32_t>(kv >> 32);
     bool lose = false;
-    for (int32_t i = threadIdx.x; i < pc; i += kBlock) {
-        const int32_t u = __ldg(lst + i);
-        if (u < 0 || u >= a.g.n) {
-            atomicOr(&a.ctrl->err, kErrBadGraph);
-            continue;
+    for (int32_t i0 = 0; i0 < pc; i0 += kHeavyU * kBlock) {
+        int32_t u[kHeavyU];
+        uint64_t ku[kHeavyU];
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k) {
+            const int32_t i = i0 + k * kBlock + static_cast<int32_t>(threadIdx.x);
+            u[k] = i < pc ? __ldg(lst + i) : -1;
         }
-        const uint64_t ku = __ldg(key + u);
-        if (u != it.v && static_cast<uint32_t>(ku >> 32) == tv && (ku > kv || (ku == kv && u > it.v)))
-            lose = true;
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k) {
+            const int32_t i = i0 + k * kBlock + static_cast<int32_t>(threadIdx.x);
+            ku[k] = 0;
+            if (i < pc) {
+                if (u[k] < 0 || u[k] >= a.g.n) {
+                    atomicOr(&a.ctrl->err, kErrBadGraph);
+                    u[k] = -1;
+                } else {
+                    ku[k] = __ldg(key + u[k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k)
+            if (u[k] >= 0 && u[k] != it.v && static_cast<uint32_t>(ku[k] >> 32) == tv &&
+                (ku[k] > kv || (ku[k] == kv && u[k] > it.v)))
+                lose = true;
     }
     return lose;
 }
@@ -522,7 +568,7 @@ __device__ __forceinline__ void conflict_group_tile(const SpecArgs& a, const Rou
     warp_append(leader && lose, it.beg, it.v, it.deg, &a.ctrl->cnt[par ^ 1][b], next, rt.start[b]);
 }
 
-__global__ void __launch_bounds__(kBlock) k_conflict(SpecArgs a) {
+__global__ void __launch_bounds__(kBlock, 5) k_conflict(SpecArgs a) {
     __shared__ RoundTiles rt;
     __shared__ bool s_last;
     const int32_t round = a.ctrl->round;
