@@ -488,7 +488,7 @@ struct RecolorFetch {
         unsigned ns = 32;
         for (int32_t it = 0; it < spin_limit; ++it) {
             __nanosleep(ns);
-            if (ns < 1024) ns <<= 1;
+            if (ns < 256) ns <<= 1;
             x = ld_relaxed(new_c + u);
             if (x > 0) return x;
             if ((it & 63) == 0 &&
