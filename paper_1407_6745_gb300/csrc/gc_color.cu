@@ -576,6 +576,10 @@ __global__ void __launch_bounds__(kBlock, 5) k_conflict(SpecArgs a) {
     const WorkItem* list = par ? a.list1 : a.list0;
     WorkItem* next = par ? a.list0 : a.list1;
     load_round_tiles(a.ctrl, par, rt);
+    // only the blocks with a tile take part in closing the round (a round has
+    // at least one tile: the rounds stop when the work set is empty)
+    const uint32_t participants = static_cast<uint32_t>(min(static_cast<int32_t>(gridDim.x), rt.prefix[kNB]));
+    if (blockIdx.x >= participants) return;
     unsigned long long edges = 0;
     int32_t my_max = 0;
     for (int32_t t = blockIdx.x; t < rt.prefix[kNB]; t += gridDim.x) {
@@ -613,7 +617,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_conflict(SpecArgs a) {
     // The last block to finish closes the round.
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&a.ctrl->done_blocks, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.ctrl->done_blocks, 1u) == participants - 1;
     __syncthreads();
     if (s_last && threadIdx.x == 0) {
         __threadfence();

@@ -547,10 +547,12 @@ __device__ __forceinline__ void warp_add(unsigned long long* dst, unsigned long 
     if (lane_id() == 0 && x != 0) atomicAdd(dst, x);
 }
 
+// Max of non-negative values into *dst (which starts at 0): a warp whose
+// values are all 0 adds nothing.
 __device__ __forceinline__ void warp_max(int32_t* dst, int32_t x) {
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) x = max(x, __shfl_xor_sync(kFull, x, d));
-    if (lane_id() == 0) atomicMax(dst, x);
+    if (lane_id() == 0 && x > 0) atomicMax(dst, x);
 }
 
 }  // namespace gc
