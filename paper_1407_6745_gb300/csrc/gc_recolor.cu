@@ -443,9 +443,27 @@ __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
     }
     for (int i = threadIdx.x; i < nseg; i += kBlock) s_cnt[i] = 0;
     __syncthreads();
+    // count: the segment and, for a split row, its chunk count (no row read
+    // for the others); shared-memory atomics, positions inside a segment are
+    // free (a class is an independent set)
     for (int64_t i = lo + threadIdx.x; i < hi; i += kBlock) {
-        const ScatterInfo si = scatter_info(a, static_cast<int32_t>(i));
-        if (si.sg >= 0) reserve(s_cnt, si);
+        const int32_t v = static_cast<int32_t>(i);
+        const int b = a.bucket[v];
+        int64_t key = a.old_c[v];
+        if (a.graph_of) {
+            const int32_t gi = a.graph_of[v];
+            if (a.iteration >= a.desc[gi].iterations) continue;
+            key += a.cls_base[gi];
+        }
+        const int32_t sg = a.rank_of[key] * kNB + b;
+        int32_t units = 1;
+        if (b == 0) {
+            int64_t beg;
+            int32_t deg;
+            row_of(a.g, v, beg, deg, &a.ctrl->err);
+            units = chunks_of(deg);
+        }
+        atomicAdd(&s_cnt[sg], units);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nseg; i += kBlock) {
@@ -461,7 +479,7 @@ __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
             a.new_c[v] = a.old_c[v];
             continue;
         }
-        const int32_t off = reserve(s_cnt, si);
+        const int32_t off = atomicAdd(&s_cnt[si.sg], si.units);
         place(a, v, si, s_base[si.sg] + off);
     }
 }
