@@ -711,10 +711,9 @@ gc_status build_rounds_graph(const SpecArgs& a, int32_t X, int grid_t, int grid_
 
 gc_status launch_rounds_graph(RoundsGraph& rg, cudaStream_t s) {
     prof_begin(KID_SPEC_GRAPH, s);
-    cudaError_t e = cudaGraphLaunch(rg.exec, s);
+    const cudaError_t e = cudaGraphLaunch(rg.exec, s);
     prof_end(KID_SPEC_GRAPH, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    return cuda_status(e);
+    return cuda_status(e);  // the caller's read-back of the round state waits for it
 }
 
 // The speculative coloring; with graph_of / desc / win_round set, a batch.

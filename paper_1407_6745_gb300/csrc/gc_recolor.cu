@@ -928,16 +928,29 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
     a.ctrl = sc_ctrl.as<RcCtrl>();
     cudaMemsetAsync(a.ctrl, 0, sizeof(RcCtrl), s);
     RcCtrl h;
+    std::memset(&h, 0, sizeof(h));
     if (n > 0) {
         GC_LAUNCH(KID_RC_BUCKET, s, k_rc_bucket<<<vgrid, kBlock, 0, s>>>(a));
         if (!trusted) GC_LAUNCH(KID_RC_VALIDATE, s, k_rc_validate<<<grid, kBlock, 0, s>>>(a));
     }
-    ce = cudaMemcpyAsync(&h, a.ctrl, sizeof(RcCtrl), cudaMemcpyDeviceToHost, s);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-    if (ce != cudaSuccess) return cuda_status(ce);
-    if (h.err & kErrBadGraph) return GC_ERR_BAD_GRAPH;
-    if (h.err & kErrImproper) return GC_ERR_IMPROPER_INPUT;
-    if (!trusted) maxc_in = h.max_in;
+    // A trusted input (our own coloring) has a known max color; the split
+    // rows are then sized by a bound (a bucket-0 row has more than
+    // max(rc_warp_max_deg, 63) entries) instead of a read-back, when the
+    // bound's scratch is small.
+    const int64_t heavy_min = std::max<int64_t>(tune.warp_max_deg, 63) + 1;
+    const int64_t heavy_bound = std::min<int64_t>(n, static_cast<int64_t>(g.nnz) / heavy_min);
+    const int64_t bound_words = (static_cast<int64_t>(std::max(maxc_in, 1)) + 1 + 31) / 32;
+    const bool read_back = !trusted || n == 0 || heavy_bound * bound_words * 4 > (int64_t(64) << 20);
+    if (read_back) {
+        ce = cudaMemcpyAsync(&h, a.ctrl, sizeof(RcCtrl), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) return cuda_status(ce);
+        if (h.err & kErrBadGraph) return GC_ERR_BAD_GRAPH;
+        if (h.err & kErrImproper) return GC_ERR_IMPROPER_INPUT;
+        if (!trusted) maxc_in = h.max_in;
+    } else {
+        h.n_heavy = static_cast<int32_t>(heavy_bound);
+    }
     if (n == 0) {
         if (ncolors_per_iter)
             for (int32_t i = 0; i <= iterations; ++i) ncolors_per_iter[i] = 0;
