@@ -169,6 +169,7 @@ gc_status gc_recolor(const gc_graph* g, const int32_t* colors_in, gc_perm perm,
  * conflicts.  Arguments, memory and errors as gc_color.
  */
 typedef enum { GC_ORDER_RANDOM = 0, GC_ORDER_LARGEST_FIRST = 1 } gc_order;
+/* GC_ERR_INVALID_ARG for an unknown order; otherwise as gc_color. */
 gc_status gc_color_ordered(const gc_graph* g, gc_strategy strategy, int32_t X, uint64_t seed,
                            gc_order order, int32_t* colors_out, gc_stats* stats, void* stream);
 
@@ -428,6 +429,7 @@ typedef struct {
     double ms;
 } gc_kernel_time;
 
+/* on != 0 starts (and resets) the per-kernel timing, 0 stops it. */
 void gc_profile_enable(int32_t on);
 /* Copies up to max entries (kernels launched at least once) into out and
  * returns how many there are. */
@@ -439,6 +441,7 @@ int32_t gc_profile_read(gc_kernel_time* out, int32_t max);
 gc_status gc_preset_params(gc_preset preset, int32_t* strategy, int32_t* X, int32_t* perm,
                            int32_t* iterations);
 
+/* A static, human-readable description of a status code (never NULL). */
 const char* gc_status_string(gc_status s);
 
 /* Library version, major * 10000 + minor * 100 + patch. */
