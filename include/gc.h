@@ -367,7 +367,7 @@ gc_status gc_check_graph(const gc_graph* g, int64_t* first_bad_vertex, void* str
 /*
  * Scheduling knobs (not part of the method: results are identical for every
  * setting).  A vertex of degree d with d + X <= 64 is handled by a group of
- * 4 lanes if d <= g4_max_deg, 8 if d <= g8_max_deg, 16 if d <= g16_max_deg,
+ * 2 lanes if d <= g2_max_deg, 4 lanes if d <= g4_max_deg, 8 if d <= g8_max_deg, 16 if d <= g16_max_deg,
  * else 32; otherwise by one warp with a shared-memory bitmap if
  * d <= warp_max_deg, else by a whole block (coloring) or split into chunks
  * of 256 neighbors (recoloring, where rc_warp_max_deg takes the place of
@@ -391,6 +391,7 @@ typedef struct {
     int32_t spin_limit;
     int32_t spec_graph;
     int32_t rc_warp_max_deg;
+    int32_t g2_max_deg;
 } gc_tuning;
 
 /* Sets the scheduling knobs (NULL restores the defaults).  GC_ERR_INVALID_ARG

@@ -80,7 +80,8 @@ class _KernelTime(ctypes.Structure):
 class _Tuning(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in ("g4_max_deg", "g8_max_deg", "g16_max_deg",
                                                "warp_max_deg", "grid_blocks", "recolor_mode",
-                                               "spin_limit", "spec_graph", "rc_warp_max_deg")]
+                                               "spin_limit", "spec_graph", "rc_warp_max_deg",
+                                               "g2_max_deg")]
 
 
 class _Request(ctypes.Structure):

@@ -54,6 +54,7 @@ Tuning default_tuning() {
     t.spin_limit = 1 << 20;
     t.spec_graph = 1;
     t.rc_warp_max_deg = 512;
+    t.g2_max_deg = 16;
     return t;
 }
 Tuning g_tune = default_tuning();
@@ -595,7 +596,7 @@ gc_status gc_validate_noalloc(const gc_graph* g, const int32_t* colors, gc_valid
 gc_status gc_set_tuning(const gc_tuning* t) {
     Tuning v = default_tuning();
     if (t) {
-        if (t->g4_max_deg < 0 || t->g8_max_deg < t->g4_max_deg || t->g16_max_deg < t->g8_max_deg ||
+        if (t->g2_max_deg < 0 || t->g4_max_deg < t->g2_max_deg || t->g8_max_deg < t->g4_max_deg || t->g16_max_deg < t->g8_max_deg ||
             t->warp_max_deg < 0 || t->grid_blocks < 0 || t->recolor_mode < 0 ||
             t->recolor_mode > 1 || t->spin_limit < 1 || t->spec_graph < 0 || t->spec_graph > 1 ||
             t->rc_warp_max_deg < 0)
@@ -609,6 +610,7 @@ gc_status gc_set_tuning(const gc_tuning* t) {
         v.spin_limit = t->spin_limit;
         v.spec_graph = t->spec_graph;
         v.rc_warp_max_deg = t->rc_warp_max_deg;
+        v.g2_max_deg = t->g2_max_deg;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune = v;
@@ -627,6 +629,7 @@ gc_status gc_get_tuning(gc_tuning* out) {
     out->spin_limit = t.spin_limit;
     out->spec_graph = t.spec_graph;
     out->rc_warp_max_deg = t.rc_warp_max_deg;
+    out->g2_max_deg = t.g2_max_deg;
     return GC_OK;
 }
 
@@ -670,8 +673,9 @@ gc_status gc_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64
     const int32_t groups[][3] = {{64, 64, 64}, {4, 8, 16}, {0, 0, 0}, {0, 64, 64}, {16, 32, 64}};
     const int32_t warp_max[] = {256, 1024, 2048};
     const int32_t rc_warp_max[] = {256, 512, 1024};
+    const int32_t g2_max[] = {0, 4, 8};
     const int32_t blocks_per_sm[] = {0, 2, 4};
-    for (int step = 0; step < 6 && st == GC_OK; ++step) {
+    for (int step = 0; step < 7 && st == GC_OK; ++step) {
         const int variants = step == 0 ? 5 : step == 1 ? 3 : step == 2 ? 2 : step == 3 ? 2 : 3;
         for (int i = 0; i < variants && st == GC_OK; ++i) {
             gc_tuning t = cur;
@@ -680,7 +684,8 @@ gc_status gc_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64
             else if (step == 2) t.recolor_mode = i;
             else if (step == 3) t.spec_graph = i;
             else if (step == 4) t.grid_blocks = blocks_per_sm[i] * sm_count();
-            else t.rc_warp_max_deg = rc_warp_max[i];
+            else if (step == 5) t.rc_warp_max_deg = rc_warp_max[i];
+            else t.g2_max_deg = std::min(g2_max[i], t.g4_max_deg);
             if (std::memcmp(&t, &cur, sizeof(t)) == 0) continue;
             float ms = 0.f;
             st = time_it(t, &ms);

@@ -470,7 +470,8 @@ __global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
         case 2: tentative_group_tile<32, kRXF>(a, rt, list, 2, first, round, edges); break;
         case 3: tentative_group_tile<16, kRXF>(a, rt, list, 3, first, round, edges); break;
         case 4: tentative_group_tile<8, kRXF>(a, rt, list, 4, first, round, edges); break;
-        default: tentative_group_tile<4, kRXF>(a, rt, list, 5, first, round, edges); break;
+        case 5: tentative_group_tile<4, kRXF>(a, rt, list, 5, first, round, edges); break;
+        default: tentative_group_tile<2, kRXF>(a, rt, list, 6, first, round, edges); break;
         }
     }
     warp_add(&a.ctrl->edges, edges);
@@ -608,7 +609,8 @@ __global__ void __launch_bounds__(kBlock, 5) k_conflict(SpecArgs a) {
         case 2: conflict_group_tile<32>(a, rt, list, next, par, b, first, my_max, edges); break;
         case 3: conflict_group_tile<16>(a, rt, list, next, par, 3, first, my_max, edges); break;
         case 4: conflict_group_tile<8>(a, rt, list, next, par, 4, first, my_max, edges); break;
-        default: conflict_group_tile<4>(a, rt, list, next, par, 5, first, my_max, edges); break;
+        case 5: conflict_group_tile<4>(a, rt, list, next, par, 5, first, my_max, edges); break;
+        default: conflict_group_tile<2>(a, rt, list, next, par, 6, first, my_max, edges); break;
         }
     }
     warp_add(&a.ctrl->edges, edges);

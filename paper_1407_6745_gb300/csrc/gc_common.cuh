@@ -17,11 +17,11 @@ namespace gc {
 
 constexpr int kBlock = 256;          // threads per block, every kernel
 constexpr int kWarps = kBlock / 32;
-constexpr int kNB = 6;               // degree buckets
+constexpr int kNB = 7;               // degree buckets
 // bucket b: 0 block/vertex, 1 warp/vertex + smem bitmap, 2..5 group of
 // 32/16/8/4 lanes per vertex with a 64-bit register mask
 __host__ __device__ constexpr int bucket_group(int b) {
-    return b == 0 ? kBlock : b == 1 ? 32 : b == 2 ? 32 : b == 3 ? 16 : b == 4 ? 8 : 4;
+    return b == 0 ? kBlock : b == 1 ? 32 : b == 2 ? 32 : b == 3 ? 16 : b == 4 ? 8 : b == 5 ? 4 : 2;
 }
 // vertices per block tile
 __host__ __device__ constexpr int bucket_tile(int b) {
@@ -47,6 +47,7 @@ struct Tuning {
     int32_t spin_limit;    // bounded wait iterations in the dataflow recolor
     int32_t spec_graph;    // 1: speculative rounds in a CUDA graph WHILE node; 0: host loop
     int32_t rc_warp_max_deg;  // warp_max_deg of the recoloring phase
+    int32_t g2_max_deg;    // deg <= this -> 2 lanes (0: none)
 };
 
 // The recoloring phase's view of the knobs: its own warp threshold.
@@ -57,6 +58,7 @@ __host__ __device__ inline Tuning recolor_tuning(Tuning t) {
 
 __host__ __device__ inline int bucket_of(int64_t deg, int32_t X, const Tuning& t) {
     if (deg + (int64_t)X <= 64) {
+        if (deg <= t.g2_max_deg) return 6;
         if (deg <= t.g4_max_deg) return 5;
         if (deg <= t.g8_max_deg) return 4;
         if (deg <= t.g16_max_deg) return 3;
@@ -510,7 +512,7 @@ __device__ __forceinline__ int32_t choose_block(const Graph& g, int64_t beg, int
 }
 
 // 4-id pieces per lane per batch, per group size (32/16/8/4 lanes).
-template <int G> struct LanesUnroll { static constexpr int U = G == 4 ? 2 : 1; };
+template <int G> struct LanesUnroll { static constexpr int U = (G == 4 || G == 2) ? 2 : 1; };
 
 // ---------------------------------------------------------------------------
 // Tiles: a list is cut into segments (one bucket each); segment s holds

@@ -42,7 +42,7 @@ constexpr int32_t kChunk = 256;   // neighbors per chunk of a split (heavy) row 
 
 // Vertices (or, bucket 0, row chunks) per warp tile.
 __host__ __device__ constexpr int warp_tile(int b) {
-    return b <= 2 ? 1 : b == 3 ? 2 : b == 4 ? 4 : 8;
+    return b <= 2 ? 1 : b == 3 ? 2 : b == 4 ? 4 : b == 5 ? 8 : 16;
 }
 
 struct RcCtrl {
@@ -640,7 +640,8 @@ __device__ __forceinline__ void recolor_warp_tile(const RcArgs& a, const NextHis
     case 2: recolor_group_tile<32, kDataflow>(a, f, nh, 2, first, seg_last, my_max, edges); break;
     case 3: recolor_group_tile<16, kDataflow>(a, f, nh, 3, first, seg_last, my_max, edges); break;
     case 4: recolor_group_tile<8, kDataflow>(a, f, nh, 4, first, seg_last, my_max, edges); break;
-    default: recolor_group_tile<4, kDataflow>(a, f, nh, 5, first, seg_last, my_max, edges); break;
+    case 5: recolor_group_tile<4, kDataflow>(a, f, nh, 5, first, seg_last, my_max, edges); break;
+    default: recolor_group_tile<2, kDataflow>(a, f, nh, 6, first, seg_last, my_max, edges); break;
     }
 }
 

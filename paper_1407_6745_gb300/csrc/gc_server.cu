@@ -92,7 +92,7 @@ struct Request {
 // whichever is larger, with room to spare.
 int64_t request_bytes(int64_t n, int64_t nnz, int64_t max_deg, int32_t X) {
     const int64_t classes = std::min<int64_t>(n, max_deg + X) + 2;
-    return 16 * (n + 1) + 4 * nnz + 4 * n + 64 * n + 16 * (nnz / 512 + 1) + 128 * classes + 1024;
+    return 16 * (n + 1) + 4 * nnz + 4 * n + 64 * n + 16 * (nnz / 256 + 1) + 256 * classes + 1024;
 }
 
 }  // namespace

@@ -173,6 +173,11 @@ def test_complete_graph_crosses_register_window():
     dict(grid_blocks=1, recolor_mode=1),
     dict(spec_graph=0),
     dict(spec_graph=0, grid_blocks=3, recolor_mode=1),
+    dict(g2_max_deg=8),
+    dict(g2_max_deg=64, g4_max_deg=64, g8_max_deg=64, g16_max_deg=64),
+    dict(g2_max_deg=4, recolor_mode=1),
+    dict(rc_warp_max_deg=0),
+    dict(rc_warp_max_deg=1 << 30),
 ])
 def test_results_do_not_depend_on_scheduling(knobs):
     g = gg.hubs(THRESHOLD_DEGREES[:-1], 6000, seed=8)
