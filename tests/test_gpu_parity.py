@@ -165,7 +165,8 @@ def test_complete_graph_crosses_register_window():
 
 @pytest.mark.parametrize("knobs", [
     dict(recolor_mode=1),
-    dict(g4_max_deg=0, g8_max_deg=0, g16_max_deg=0),
+    dict(g2_max_deg=0, g4_max_deg=0, g8_max_deg=0, g16_max_deg=0),
+    dict(g2_max_deg=0),
     dict(g4_max_deg=64, g8_max_deg=64, g16_max_deg=64),
     dict(warp_max_deg=0),
     dict(warp_max_deg=1 << 30),
