@@ -679,7 +679,12 @@ gc_status gc_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64
         const int variants = step == 0 ? 5 : step == 1 ? 3 : step == 2 ? 2 : step == 3 ? 2 : 3;
         for (int i = 0; i < variants && st == GC_OK; ++i) {
             gc_tuning t = cur;
-            if (step == 0) { t.g4_max_deg = groups[i][0]; t.g8_max_deg = groups[i][1]; t.g16_max_deg = groups[i][2]; }
+            if (step == 0) {
+                t.g4_max_deg = groups[i][0];
+                t.g8_max_deg = groups[i][1];
+                t.g16_max_deg = groups[i][2];
+                t.g2_max_deg = std::min(t.g2_max_deg, t.g4_max_deg);
+            }
             else if (step == 1) t.warp_max_deg = warp_max[i];
             else if (step == 2) t.recolor_mode = i;
             else if (step == 3) t.spec_graph = i;
