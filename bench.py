@@ -642,7 +642,12 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=2)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-check", type=int, default=40)
+    ap.add_argument("--tune", default="", help="scheduling knobs, e.g. g2_max_deg=0,recolor_mode=1 "
+                    "(results do not depend on them)")
     args = ap.parse_args()
+    if args.tune and args.impl != "reference":
+        import paper_1407_6745_gb300 as gc
+        gc.gc_set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tune.split(","))})
     if args.workload in ("batch", "serve") and args.impl == "reference":
         run_reference_graphs(args)
         return
