@@ -414,6 +414,11 @@ gc_status gc_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64
                       int32_t iterations, int32_t repeats, gc_tuning* best, float* best_ms,
                       void* stream);
 
+/* Testing aid (host-side fault injection; not in the paper): the scratch
+ * allocation after the next `after` ones fails once, so the call making it
+ * returns GC_ERR_OOM; after < 0 disables.  Process-wide. */
+void gc_inject_alloc_failure(int64_t after);
+
 /* Number of kernel launches the library has made in this process. */
 int64_t gc_kernel_launches(void);
 

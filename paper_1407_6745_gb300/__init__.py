@@ -26,7 +26,7 @@ __all__ = [
     "gc_server_stats", "gc_server_destroy",
     "gc_priorities", "gc_set_tuning", "gc_get_tuning", "gc_profile_enable", "gc_profile_read",
     "gc_kernel_launches", "gc_status_string", "gc_version", "gc_preset_params",
-    "gc_color_ordered", "gc_recolor_async",
+    "gc_color_ordered", "gc_recolor_async", "gc_inject_alloc_failure",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -154,6 +154,8 @@ def load():
         lib.gc_recolor_async.argtypes = [G, P, ctypes.c_int, ctypes.c_int32, ctypes.c_uint64, P, P, S, P]
         for f in ("gc_color_ordered", "gc_recolor_async"):
             getattr(lib, f).restype = ctypes.c_int
+        lib.gc_inject_alloc_failure.argtypes = [ctypes.c_int64]
+        lib.gc_inject_alloc_failure.restype = None
         lib.gc_preset_params.argtypes = [ctypes.c_int, P, P, P, P]
         lib.gc_preset_params.restype = ctypes.c_int
         lib.gc_server_destroy.argtypes = [H]
@@ -599,6 +601,12 @@ def gc_preset_params(preset):
            "gc_preset_params")
     return {"strategy": "FF" if s.value == FIRST_FIT else "RXF", "X": x.value,
             "perm": {v: k for k, v in PERM.items()}.get(p.value, p.value), "iterations": it.value}
+
+
+def gc_inject_alloc_failure(after: int):
+    """Testing aid: the library's scratch allocation after the next `after`
+    ones fails once (GC_ERR_OOM); a negative value disables."""
+    load().gc_inject_alloc_failure(int(after))
 
 
 def gc_kernel_launches() -> int:

@@ -60,7 +60,16 @@ Tuning default_tuning() {
 Tuning g_tune = default_tuning();
 }  // namespace
 
+namespace {
+// Host-side fault injection (gc_inject_alloc_failure): the allocation after
+// the next `g_fail_after` ones fails once.
+std::atomic<long long> g_fail_after{-1};
+}  // namespace
+
 void* scratch_alloc(size_t bytes, cudaStream_t s) {
+    if (g_fail_after.load(std::memory_order_relaxed) >= 0 &&
+        g_fail_after.fetch_sub(1, std::memory_order_relaxed) == 0)
+        return nullptr;
     cudaMemPool_t p = pool_for_current_device();
     if (!p) return nullptr;
     void* ptr = nullptr;
@@ -721,6 +730,8 @@ gc_status gc_preset_params(gc_preset preset, int32_t* strategy, int32_t* X, int3
     if (iterations) *iterations = i_;
     return GC_OK;
 }
+
+void gc_inject_alloc_failure(int64_t after) { g_fail_after.store(after < 0 ? -1 : after); }
 
 int64_t gc_kernel_launches(void) { return g_launches.load(); }
 

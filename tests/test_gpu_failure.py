@@ -67,3 +67,46 @@ def test_bad_inputs_are_errors_not_faults():
     c, _ = gc.gc_color(off, idx, "FF", 1, 2)
     o, i = g.numpy()
     assert np.array_equal(c.cpu().numpy(), oracle.color(o, i, 1, 2)[0])
+
+
+def _calls(g, off, idx):
+    start = torch.from_numpy(oracle.color(*g.numpy(), 3, 1)[0]).cuda()
+    u = gg.batch_union([g, gg.erdos_renyi(500, 6.0, seed=2)]).to("cuda")
+    desc = [dict(n=g.n, seed=1, X=3, perm="NI", iterations=2), dict(n=500, seed=2, perm="RAND", iterations=1)]
+    return [
+        ("color_recolor", lambda: gc.gc_color_recolor(off, idx, "RXF", 3, 1, "NI", 2, 0, validate=True)[0]),
+        ("recolor", lambda: gc.gc_recolor(off, idx, start, "RAND", 2, 5)[0]),
+        ("color_host", lambda: gc.gc_color(off.cpu(), idx.cpu(), "FF", 1, 2)[0]),
+        ("lf", lambda: gc.gc_color_ordered(off, idx, "FF", 1, 2, "LF")[0]),
+        ("arc", lambda: gc.gc_recolor_async(off, idx, start, "ND", 2, 1)[0]),
+        ("validate", lambda: gc.gc_validate(off, idx, start)),
+        ("batch", lambda: gc.gc_color_recolor_batch(u.offsets, u.idx, desc)[0]),
+    ]
+
+
+def test_allocation_failures_are_reported_and_harmless():
+    """Host-side fault injection: the k-th scratch allocation of a call fails.
+    Every entry point returns GC_ERR_OOM (or succeeds when it allocates fewer
+    than k times), and the next call gives the right answer."""
+    g = gg.workload("rmat10")  # split rows and heavy rows on both phases
+    off, idx = g.offsets.cuda(), g.idx.cuda()
+    for name, call in _calls(g, off, idx):
+        ref = call()
+        ref = ref if isinstance(ref, dict) else ref.clone()
+        for k in range(0, 40):
+            gc.gc_inject_alloc_failure(k)
+            try:
+                call()
+                failed = False
+            except gc.GCError as e:
+                assert e.name == "GC_ERR_OOM", (name, k, e.name)
+                failed = True
+            finally:
+                gc.gc_inject_alloc_failure(-1)
+            again = call()
+            if isinstance(ref, dict):
+                assert again == ref, (name, k)
+            else:
+                assert torch.equal(again, ref), (name, k)
+            if not failed:
+                break  # the call makes fewer than k + 1 allocations
