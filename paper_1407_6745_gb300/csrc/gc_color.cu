@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kHeavyThreads) k_heavy_setup(SpecArgs a, int32
         if (h < nh) {
             const WorkItem it = load_item(a.list0 + start0 + h);
             v = it.v;
-            e = it.deg;
+            e = (static_cast<long long>(it.deg) + 3) & ~3ll;  // 16-byte aligned list starts
             wd = heavy_words(it.deg);
         }
         long long ie = e, iw = wd;  // warp inclusive scans
@@ -322,8 +322,30 @@ __device__ __forceinline__ void tentative_group_tile(const SpecArgs& a, const Ro
 // takes the j-th permissible color from the bitmap.  Past the bitmap's free
 // colors (Random-X with a large X) the row is scanned in full instead.
 constexpr int kHeavyU = 4;  // pending entries per thread per step of a heavy row
+constexpr int kHeavyStep = kHeavyU * kBlock;
 
-__device__ int32_t choose_heavy(const SpecArgs& a, const WorkItem& it, uint32_t j, SpecShared& sm) {
+// Per-thread asynchronous 16-byte global -> shared copies (cp.async): a
+// thread stages the 4 list entries it will process next while it works on
+// the current ones, and waits only for its own copies (no barrier, no spin).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Stages step `step` of a 16-byte aligned pending list (entries [i0, i0 +
+// kHeavyStep), thread t the 4 at i0 + 4t) into buf.  A copy may read up to 3
+// entries past cnt: lists are padded to 4 entries.
+__device__ __forceinline__ void stage_step(int32_t* buf, const int32_t* lst, int64_t i0, int64_t cnt) {
+    const int64_t i = i0 + 4 * static_cast<int64_t>(threadIdx.x);
+    if (i < cnt) cp_async16(buf + 4 * threadIdx.x, lst + i);
+    cp_async_commit();
+}
+
+__device__ int32_t choose_heavy(const SpecArgs& a, const WorkItem& it, uint32_t j, SpecShared& sm,
+                                int32_t (*stage)[kHeavyStep]) {
     const int t = threadIdx.x, l = lane_id(), w = t >> 5;
     const HeavyRows hr = *a.heavy;
     const int32_t h = hr.hid[it.v];
@@ -342,22 +364,10 @@ __device__ int32_t choose_heavy(const SpecArgs& a, const WorkItem& it, uint32_t 
     for (int i = t; i < sw; i += kBlock) sm.blk.bm[i] = 0u;
     __syncthreads();
     int32_t kept = 0;
-    for (int64_t i0 = 0; i0 < cnt; i0 += static_cast<int64_t>(kHeavyU) * kBlock) {
-        int32_t u[kHeavyU], c[kHeavyU];
-#pragma unroll
-        for (int k = 0; k < kHeavyU; ++k) {  // all loads of the step in flight together
-            const int64_t i = i0 + static_cast<int64_t>(k) * kBlock + t;
-            u[k] = i < cnt ? src[i] : -1;
-        }
-#pragma unroll
-        for (int k = 0; k < kHeavyU; ++k) {
-            const int64_t i = i0 + static_cast<int64_t>(k) * kBlock + t;
-            c[k] = -1;  // -1: no entry
-            if (i < cnt) {
-                if (u[k] < 0 || u[k] >= a.g.n) atomicOr(&a.ctrl->err, kErrBadGraph);
-                else c[k] = __ldg(a.color + u[k]);
-            }
-        }
+    // one step: the kHeavyU entries u[] of this thread; fold the colored ones,
+    // keep the others (written after the step's barrier, at or below every
+    // position read in the step)
+    auto step_done = [&](const int32_t (&u)[kHeavyU], const int32_t (&c)[kHeavyU]) {
         int32_t mine = 0;
 #pragma unroll
         for (int k = 0; k < kHeavyU; ++k) {
@@ -379,12 +389,56 @@ __device__ int32_t choose_heavy(const SpecArgs& a, const WorkItem& it, uint32_t 
             if (k < w) before += x;
             total += x;
         }
-        int32_t pos = kept + before + incl_w - mine;  // at or below every position read this step
+        int32_t pos = kept + before + incl_w - mine;
 #pragma unroll
         for (int k = 0; k < kHeavyU; ++k)
             if (c[k] == 0) dst[pos++] = u[k];
         kept += total;
         __syncthreads();
+    };
+    if (pc < 0) {  // first look: the row itself (any alignment), strided loads
+        for (int64_t i0 = 0; i0 < cnt; i0 += kHeavyStep) {
+            int32_t u[kHeavyU], c[kHeavyU];
+#pragma unroll
+            for (int k = 0; k < kHeavyU; ++k) {
+                const int64_t i = i0 + static_cast<int64_t>(k) * kBlock + t;
+                u[k] = i < cnt ? src[i] : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < kHeavyU; ++k) {
+                const int64_t i = i0 + static_cast<int64_t>(k) * kBlock + t;
+                c[k] = -1;  // -1: no entry
+                if (i < cnt) {
+                    if (u[k] < 0 || u[k] >= a.g.n) atomicOr(&a.ctrl->err, kErrBadGraph);
+                    else c[k] = __ldg(a.color + u[k]);
+                }
+            }
+            step_done(u, c);
+        }
+    } else {  // the pending list (16-byte aligned): the next step staged while this one runs
+        if (cnt > 0) stage_step(stage[0], src, 0, cnt);
+        int parity = 0;
+        for (int64_t i0 = 0; i0 < cnt; i0 += kHeavyStep, parity ^= 1) {
+            const bool more = i0 + kHeavyStep < cnt;
+            if (more) stage_step(stage[parity ^ 1], src, i0 + kHeavyStep, cnt);
+            if (more) cp_async_wait<1>(); else cp_async_wait<0>();
+            int32_t u[kHeavyU], c[kHeavyU];
+#pragma unroll
+            for (int k = 0; k < kHeavyU; ++k) {
+                const int64_t i = i0 + 4 * static_cast<int64_t>(t) + k;
+                u[k] = i < cnt ? stage[parity][4 * t + k] : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < kHeavyU; ++k) {
+                const int64_t i = i0 + 4 * static_cast<int64_t>(t) + k;
+                c[k] = -1;
+                if (i < cnt) {
+                    if (u[k] < 0 || u[k] >= a.g.n) atomicOr(&a.ctrl->err, kErrBadGraph);
+                    else c[k] = __ldg(a.color + u[k]);
+                }
+            }
+            step_done(u, c);  // its barriers also free stage[parity] for the step after next
+        }
     }
     for (int i = t; i < sw; i += kBlock) {
         const uint32_t x = sm.blk.bm[i];
@@ -426,6 +480,7 @@ template <bool kRXF>
 __global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
     __shared__ SpecShared sm;
     __shared__ RoundTiles rt;
+    __shared__ __align__(16) int32_t stage[2][kHeavyStep];  // heavy rows' next list step
     const int32_t round = a.ctrl->round;
     const int par = round & 1;
     const WorkItem* list = par ? a.list1 : a.list0;
@@ -445,7 +500,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
         case 0: {
             const WorkItem it = load_item(list + rt.start[0] + first);
             const uint32_t j = kRXF ? draw_index(a, it.v, round) : 0u;
-            int32_t c = choose_heavy(a, it, j, sm);  // rounds >= 1
+            int32_t c = choose_heavy(a, it, j, sm, stage);  // rounds >= 1
             if (c < 0) c = choose_block<4>(a.g, it.beg, it.deg, j, fetch, sm.blk, &a.ctrl->err);
             if (threadIdx.x == 0) {
                 set_tent(a, it.v, c);
@@ -505,27 +560,30 @@ __device__ __forceinline__ bool loses(const SpecArgs& a, const WorkItem& it, int
 
 // The same test for a heavy row after round 0, over its pending list: the
 // neighbors uncolored before the round, the only ones that can share its
-// tentative color.
-__device__ __forceinline__ bool loses_pending(const SpecArgs& a, const WorkItem& it) {
+// tentative color.  The list's next step is staged while this one runs.
+__device__ __forceinline__ bool loses_pending(const SpecArgs& a, const WorkItem& it,
+                                              int32_t (*stage)[kHeavyStep]) {
     const HeavyRows hr = *a.heavy;
     const int32_t h = hr.hid[it.v];
-    const int32_t pc = hr.h_pcnt[h];
+    const int64_t pc = hr.h_pcnt[h];
     const int32_t* lst = hr.pend + hr.h_pbeg[h];
     const unsigned long long* key = reinterpret_cast<const unsigned long long*>(a.key);
     const uint64_t kv = __ldg(key + it.v);
     const uint32_t tv = static_cast<uint32_t>(kv >> 32);
+    const int t = threadIdx.x;
     bool lose = false;
-    for (int32_t i0 = 0; i0 < pc; i0 += kHeavyU * kBlock) {
+    if (pc > 0) stage_step(stage[0], lst, 0, pc);
+    int parity = 0;
+    for (int64_t i0 = 0; i0 < pc; i0 += kHeavyStep, parity ^= 1) {
+        const bool more = i0 + kHeavyStep < pc;
+        if (more) stage_step(stage[parity ^ 1], lst, i0 + kHeavyStep, pc);
+        if (more) cp_async_wait<1>(); else cp_async_wait<0>();
         int32_t u[kHeavyU];
         uint64_t ku[kHeavyU];
 #pragma unroll
         for (int k = 0; k < kHeavyU; ++k) {
-            const int32_t i = i0 + k * kBlock + static_cast<int32_t>(threadIdx.x);
-            u[k] = i < pc ? __ldg(lst + i) : -1;
-        }
-#pragma unroll
-        for (int k = 0; k < kHeavyU; ++k) {
-            const int32_t i = i0 + k * kBlock + static_cast<int32_t>(threadIdx.x);
+            const int64_t i = i0 + 4 * static_cast<int64_t>(t) + k;
+            u[k] = i < pc ? stage[parity][4 * t + k] : -1;
             ku[k] = 0;
             if (i < pc) {
                 if (u[k] < 0 || u[k] >= a.g.n) {
@@ -572,6 +630,7 @@ __device__ __forceinline__ void conflict_group_tile(const SpecArgs& a, const Rou
 __global__ void __launch_bounds__(kBlock, 5) k_conflict(SpecArgs a) {
     __shared__ RoundTiles rt;
     __shared__ bool s_last;
+    __shared__ __align__(16) int32_t stage[2][kHeavyStep];  // heavy rows' next list step
     const int32_t round = a.ctrl->round;
     const int par = round & 1;
     const WorkItem* list = par ? a.list1 : a.list0;
@@ -589,7 +648,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_conflict(SpecArgs a) {
         switch (b) {
         case 0: {
             const WorkItem it = load_item(list + rt.start[0] + first);
-            const bool mine = round == 0 ? loses<1>(a, it, threadIdx.x, kBlock) : loses_pending(a, it);
+            const bool mine = round == 0 ? loses<1>(a, it, threadIdx.x, kBlock) : loses_pending(a, it, stage);
             const bool lose = __syncthreads_or(mine);
             if (threadIdx.x == 0) {
                 edges += static_cast<unsigned long long>(it.deg);
