@@ -476,6 +476,85 @@ __device__ int32_t choose_heavy(const SpecArgs& a, const WorkItem& it, uint32_t 
     return -1;  // past the bitmap
 }
 
+// Warp-bucket row v in round >= 1 (the whole warp): the warp-scale form of
+// choose_heavy.  New forbidden colors gather in the warp's shared window
+// (2048 colors) and merge into the row's global bitmap; kept ids are
+// compacted in place with ballots (a step's reads precede its writes, which
+// land at or below every position it read).  -1: past the bitmap.
+__device__ int32_t choose_warp_pending(const SpecArgs& a, const WorkItem& it, uint32_t j, uint32_t* sbm) {
+    const int l = lane_id();
+    const HeavyRows hr = *a.heavy;
+    const int32_t h = hr.hid[it.v];
+    const int32_t pc = hr.h_pcnt[h];
+    const int64_t cnt = pc < 0 ? static_cast<int64_t>(it.deg) : static_cast<int64_t>(pc);
+    const int32_t* src = pc < 0 ? a.g.idx + it.beg : hr.pend + hr.h_pbeg[h];
+    int32_t* dst = hr.pend + hr.h_pbeg[h];
+    uint32_t* bm = hr.hbm + hr.h_bbeg[h];
+    const int32_t words = hr.h_bwords[h];
+    const uint32_t bits = 32u * static_cast<uint32_t>(words);
+    const int32_t sw = min(words, kWarpBitmapWords);
+    const uint32_t sbits = 32u * static_cast<uint32_t>(sw);
+    for (int i = l; i < sw; i += 32) sbm[i] = 0u;
+    __syncwarp();
+    int32_t kept = 0;
+    for (int64_t i0 = 0; i0 < cnt; i0 += kHeavyU * 32) {
+        int32_t u[kHeavyU], c[kHeavyU];
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k) {
+            const int64_t i = i0 + k * 32 + l;
+            u[k] = i < cnt ? src[i] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k) {
+            const int64_t i = i0 + k * 32 + l;
+            c[k] = -1;
+            if (i < cnt) {
+                if (u[k] < 0 || u[k] >= a.g.n) atomicOr(&a.ctrl->err, kErrBadGraph);
+                else c[k] = __ldg(a.color + u[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k) {
+            if (c[k] > 0) {
+                const uint32_t b = static_cast<uint32_t>(c[k] - 1);
+                if (b < sbits) atomicOr(&sbm[b >> 5], 1u << (b & 31));
+                else if (b < bits) atomicOr(bm + (b >> 5), 1u << (b & 31));
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k) {
+            const unsigned bal = __ballot_sync(kFull, c[k] == 0);
+            if (c[k] == 0) dst[kept + __popc(bal & ((1u << l) - 1u))] = u[k];
+            kept += __popc(bal);
+        }
+    }
+    if (l == 0) hr.h_pcnt[h] = kept;
+    __syncwarp();
+    for (int i = l; i < sw; i += 32) {
+        const uint32_t x = sbm[i];
+        if (x) bm[i] = __ldcg(bm + i) | x;  // the warp owns these words this round
+    }
+    __syncwarp();
+    for (int32_t w0 = 0; w0 < words; w0 += 32) {
+        const int32_t wi = w0 + l;
+        const uint32_t f = wi < words ? ~__ldcg(bm + wi) : 0u;
+        const uint32_t cnt_f = static_cast<uint32_t>(__popc(f));
+        const uint32_t incl = warp_inclusive_scan(cnt_f);
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        if (j < total) {
+            const uint32_t excl = incl - cnt_f;
+            const bool mine = j >= excl && j < incl;
+            const int owner = __ffs(__ballot_sync(kFull, mine)) - 1;
+            int32_t color = 0;
+            if (mine) color = 32 * wi + select_bit32(f, j - excl) + 1;
+            return __shfl_sync(kFull, color, owner);
+        }
+        j -= total;
+    }
+    return -1;  // past the bitmap
+}
+
 template <bool kRXF>
 __global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
     __shared__ SpecShared sm;
@@ -514,7 +593,8 @@ __global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
             if (k < rt.cnt[1]) {
                 const WorkItem it = load_item(list + rt.start[1] + k);
                 const uint32_t j = kRXF ? draw_index(a, it.v, round) : 0u;
-                const int32_t c = choose_warp<4>(a.g, it.beg, it.deg, j, fetch, sm.warp_bm[w], &a.ctrl->err);
+                int32_t c = choose_warp_pending(a, it, j, sm.warp_bm[w]);  // rounds >= 1
+                if (c < 0) c = choose_warp<4>(a.g, it.beg, it.deg, j, fetch, sm.warp_bm[w], &a.ctrl->err);
                 if (lane_id() == 0) {
                     set_tent(a, it.v, c);
                     edges += static_cast<unsigned long long>(it.deg);
@@ -603,7 +683,46 @@ __device__ __forceinline__ bool loses_pending(const SpecArgs& a, const WorkItem&
     return lose;
 }
 
-template <int G>
+// The conflict test of a warp-bucket row after round 0, over its pending
+// list (the whole warp).
+__device__ __forceinline__ bool loses_pending_warp(const SpecArgs& a, const WorkItem& it) {
+    const HeavyRows hr = *a.heavy;
+    const int32_t h = hr.hid[it.v];
+    const int32_t pc = hr.h_pcnt[h];
+    const int32_t* lst = hr.pend + hr.h_pbeg[h];
+    const unsigned long long* key = reinterpret_cast<const unsigned long long*>(a.key);
+    const uint64_t kv = __ldg(key + it.v);
+    const uint32_t tv = static_cast<uint32_t>(kv >> 32);
+    const int l = lane_id();
+    bool lose = false;
+    for (int32_t i0 = 0; i0 < pc; i0 += kHeavyU * 32) {
+        int32_t u[kHeavyU];
+        uint64_t ku[kHeavyU];
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k) {
+            const int32_t i = i0 + k * 32 + l;
+            u[k] = i < pc ? __ldg(lst + i) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k) {
+            ku[k] = 0;
+            if (u[k] >= a.g.n) {
+                atomicOr(&a.ctrl->err, kErrBadGraph);
+                u[k] = -1;
+            } else if (u[k] >= 0) {
+                ku[k] = __ldg(key + u[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kHeavyU; ++k)
+            if (u[k] >= 0 && u[k] != it.v && static_cast<uint32_t>(ku[k] >> 32) == tv &&
+                (ku[k] > kv || (ku[k] == kv && u[k] > it.v)))
+                lose = true;
+    }
+    return __any_sync(kFull, lose);
+}
+
+template <int G, bool kPending = false>
 __device__ __forceinline__ void conflict_group_tile(const SpecArgs& a, const RoundTiles& rt,
                                                     const WorkItem* list, WorkItem* next, int par,
                                                     int b, int32_t first, int32_t& my_max,
@@ -613,7 +732,9 @@ __device__ __forceinline__ void conflict_group_tile(const SpecArgs& a, const Rou
     const bool valid = k < rt.cnt[b];
     WorkItem it{0, 0, 0};
     if (valid) it = load_item(list + rt.start[b] + k);
-    const bool lose = group_any<G>(loses<LanesUnroll<G>::U>(a, it, gl, G));
+    bool lose;
+    if constexpr (kPending) lose = valid && loses_pending_warp(a, it);  // G == 32: one warp per row
+    else lose = group_any<G>(loses<LanesUnroll<G>::U>(a, it, gl, G));
     const bool leader = valid && gl == 0;
     if (leader) {
         edges += static_cast<unsigned long long>(it.deg);
@@ -665,7 +786,10 @@ __global__ void __launch_bounds__(kBlock, 5) k_conflict(SpecArgs a) {
             break;
         }
         case 1:
-        case 2: conflict_group_tile<32>(a, rt, list, next, par, b, first, my_max, edges); break;
+            if (round == 0) conflict_group_tile<32>(a, rt, list, next, par, 1, first, my_max, edges);
+            else conflict_group_tile<32, true>(a, rt, list, next, par, 1, first, my_max, edges);
+            break;
+        case 2: conflict_group_tile<32>(a, rt, list, next, par, 2, first, my_max, edges); break;
         case 3: conflict_group_tile<16>(a, rt, list, next, par, 3, first, my_max, edges); break;
         case 4: conflict_group_tile<8>(a, rt, list, next, par, 4, first, my_max, edges); break;
         case 5: conflict_group_tile<4>(a, rt, list, next, par, 5, first, my_max, edges); break;
@@ -854,7 +978,7 @@ static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int3
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) return cuda_status(ce);
         if (h0.err) return status_from_err_bits(h0.err);
-        const int32_t nh = h0.init_cnt[0];
+        const int32_t nh = h0.init_cnt[0] + h0.init_cnt[1];  // block- and warp-bucket rows
         if (nh > 0) {
             if (!sc_hid.alloc(n * 4, s) || !sc_pbeg.alloc(static_cast<int64_t>(nh) * 8, s) ||
                 !sc_pcnt.alloc(static_cast<int64_t>(nh) * 4, s) || !sc_bbeg.alloc(static_cast<int64_t>(nh) * 8, s) ||
