@@ -184,26 +184,83 @@ __global__ void __launch_bounds__(kBlock) k_spec_fill(SpecArgs a) {
 // Heavy rows: index, pending-list and bitmap offsets (exclusive scans over
 // the bucket-0 region of the round-0 list), one block.
 constexpr int kHeavyThreads = 1024;
-__global__ void __launch_bounds__(kHeavyThreads) k_heavy_setup(SpecArgs a, int32_t nh) {
+constexpr int kHeavyChunk = 8 * kHeavyThreads;  // rows per block of the two set-up kernels
+
+__device__ __forceinline__ void heavy_sizes(const SpecArgs& a, int32_t h, int32_t nh, int32_t& v,
+                                            long long& e, long long& wd) {
+    v = 0;
+    e = 0;
+    wd = 0;
+    if (h < nh) {
+        const WorkItem it = load_item(a.list0 + a.ctrl->start[0] + h);
+        v = it.v;
+        e = (static_cast<long long>(it.deg) + 3) & ~3ll;  // 16-byte aligned list starts
+        wd = heavy_words(it.deg);
+    }
+}
+
+// Block sums of the list entries and bitmap words of its chunk of rows.
+__global__ void __launch_bounds__(kHeavyThreads) k_heavy_sums(SpecArgs a, int32_t nh, long long* sums) {
+    __shared__ long long s_e[kHeavyThreads / 32], s_w[kHeavyThreads / 32];
+    const int l = lane_id(), w = threadIdx.x >> 5;
+    long long te = 0, tw = 0;
+    const int32_t lo = blockIdx.x * kHeavyChunk;
+    for (int32_t h = lo + static_cast<int32_t>(threadIdx.x); h < min(nh, lo + kHeavyChunk); h += kHeavyThreads) {
+        int32_t v;
+        long long e, wd;
+        heavy_sizes(a, h, nh, v, e, wd);
+        te += e;
+        tw += wd;
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        te += __shfl_xor_sync(kFull, te, d);
+        tw += __shfl_xor_sync(kFull, tw, d);
+    }
+    if (l == 0) {
+        s_e[w] = te;
+        s_w[w] = tw;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long be = 0, bw = 0;
+        for (int k = 0; k < kHeavyThreads / 32; ++k) {
+            be += s_e[k];
+            bw += s_w[k];
+        }
+        sums[2 * blockIdx.x] = be;
+        sums[2 * blockIdx.x + 1] = bw;
+    }
+}
+
+// Heavy rows: index, pending-list and bitmap offsets (exclusive scans over
+// the block- and warp-bucket regions of the round-0 list), a chunk of rows
+// per block, based at the sums of the chunks before it.
+__global__ void __launch_bounds__(kHeavyThreads) k_heavy_setup(SpecArgs a, int32_t nh, const long long* sums) {
     __shared__ long long s_e[kHeavyThreads / 32], s_w[kHeavyThreads / 32];
     __shared__ long long s_base_e, s_base_w;
     const int l = lane_id(), w = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
-        s_base_e = 0;
-        s_base_w = 0;
+        long long be = 0, bw = 0;
+        for (uint32_t b = 0; b < blockIdx.x; ++b) {
+            be += sums[2 * b];
+            bw += sums[2 * b + 1];
+        }
+        s_base_e = be;
+        s_base_w = bw;
+        if (blockIdx.x == gridDim.x - 1) {
+            a.ctrl->heavy_entries = be + sums[2 * blockIdx.x];
+            a.ctrl->heavy_words = bw + sums[2 * blockIdx.x + 1];
+        }
     }
     __syncthreads();
-    const int32_t start0 = a.ctrl->start[0];
-    for (int32_t h0 = 0; h0 < nh; h0 += kHeavyThreads) {
+    const int32_t lo = blockIdx.x * kHeavyChunk;
+    const int32_t hi = min(nh, lo + kHeavyChunk);
+    for (int32_t h0 = lo; h0 < hi; h0 += kHeavyThreads) {
         const int32_t h = h0 + static_cast<int32_t>(threadIdx.x);
-        long long e = 0, wd = 0;
-        int32_t v = 0;
-        if (h < nh) {
-            const WorkItem it = load_item(a.list0 + start0 + h);
-            v = it.v;
-            e = (static_cast<long long>(it.deg) + 3) & ~3ll;  // 16-byte aligned list starts
-            wd = heavy_words(it.deg);
-        }
+        int32_t v;
+        long long e, wd;
+        heavy_sizes(a, h < hi ? h : nh, nh, v, e, wd);
         long long ie = e, iw = wd;  // warp inclusive scans
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -227,7 +284,7 @@ __global__ void __launch_bounds__(kHeavyThreads) k_heavy_setup(SpecArgs a, int32
             te += s_e[k];
             tw += s_w[k];
         }
-        if (h < nh) {
+        if (h < hi) {
             const HeavyRows& hr = *a.heavy;
             hr.hid[v] = h;
             hr.h_pbeg[h] = be + ie - e;
@@ -241,10 +298,6 @@ __global__ void __launch_bounds__(kHeavyThreads) k_heavy_setup(SpecArgs a, int32
             s_base_w += tw;
         }
         __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        a.ctrl->heavy_entries = s_base_e;
-        a.ctrl->heavy_words = s_base_w;
     }
 }
 
@@ -971,7 +1024,7 @@ static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int3
     RoundsGraph rg;
     if (a.tune.spec_graph && (st = build_rounds_graph(a, X, grid_t, grid_c, rg)) != GC_OK) return st;
     // heavy rows: their pending lists and bitmaps (sizes read back)
-    Scratch sc_hid, sc_pbeg, sc_pcnt, sc_bbeg, sc_bwords, sc_pend, sc_hbm;
+    Scratch sc_hid, sc_pbeg, sc_pcnt, sc_bbeg, sc_bwords, sc_pend, sc_hbm, sc_hsums;
     {
         SpecCtrl h0;
         cudaError_t ce = cudaMemcpyAsync(&h0, a.ctrl, sizeof(SpecCtrl), cudaMemcpyDeviceToHost, s);
@@ -992,7 +1045,11 @@ static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int3
             hr1.h_bwords = sc_bwords.as<int32_t>();
             ce = cudaMemcpyAsync(a.heavy, &hr1, sizeof(HeavyRows), cudaMemcpyHostToDevice, s);
             if (ce != cudaSuccess) return cuda_status(ce);
-            GC_LAUNCH(KID_SPEC_FILL, s, k_heavy_setup<<<1, kHeavyThreads, 0, s>>>(a, nh));
+            const int hblocks = static_cast<int>((static_cast<int64_t>(nh) + kHeavyChunk - 1) / kHeavyChunk);
+            if (!sc_hsums.alloc(static_cast<int64_t>(hblocks) * 16, s)) return GC_ERR_OOM;
+            GC_LAUNCH(KID_SPEC_FILL, s, k_heavy_sums<<<hblocks, kHeavyThreads, 0, s>>>(a, nh, sc_hsums.as<long long>()));
+            GC_LAUNCH(KID_SPEC_FILL, s,
+                      k_heavy_setup<<<hblocks, kHeavyThreads, 0, s>>>(a, nh, sc_hsums.as<long long>()));
             ce = cudaMemcpyAsync(&h0, a.ctrl, sizeof(SpecCtrl), cudaMemcpyDeviceToHost, s);
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
             if (ce != cudaSuccess) return cuda_status(ce);
