@@ -378,8 +378,8 @@ gc_status gc_check_graph(const gc_graph* g, int64_t* first_bad_vertex, void* str
  * spec_graph 1 (default) runs the speculative rounds as a CUDA graph whose
  * WHILE node repeats {tentative, conflict} until a kernel reports an empty
  * work set (no host round trip per round); 0 drives the rounds from the
- * host.  The setting is process-wide; change it only while no call is
- * running.
+ * host.  gc_set_tuning sets the process-wide knobs (change them only while
+ * no call is running); a plan's knobs apply to its own calls only.
  */
 typedef struct {
     int32_t g4_max_deg;
@@ -403,16 +403,67 @@ gc_status gc_get_tuning(gc_tuning* out);
 /*
  * Autotuner: times gc_color_recolor on the caller's graph (device memory) for
  * candidate scheduling knobs, by coordinate descent from the knobs in force
- * (lane-group thresholds, warp_max_deg, recolor_mode, spec_graph, grid size),
+ * for the calling thread (lane-group thresholds, warp_max_deg,
+ * rc_warp_max_deg, g2_max_deg, recolor_mode, spec_graph, grid size),
  * `repeats` timed runs each after one warm-up, and returns the fastest in
  * `best` with its time.  Results are identical for every candidate, so only
- * speed is compared.  The knobs in force are restored before returning; the
- * caller applies `best` with gc_set_tuning.  (A library convenience, not in
- * the paper.)
+ * speed is compared.  The candidates are applied to the calling thread only:
+ * the process-wide knobs, and calls running on other threads, are never
+ * touched.  The caller applies `best` with gc_set_tuning or keeps it in a
+ * plan (below).  GC_ERR_INVALID_ARG unless the graph is in device memory
+ * with n >= 1 and repeats >= 1.  (A library convenience, not in the paper.)
  */
 gc_status gc_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64_t seed, gc_perm perm,
                       int32_t iterations, int32_t repeats, gc_tuning* best, float* best_ms,
                       void* stream);
+
+/*
+ * Plans (a library convenience, not in the paper).  A plan is an opaque,
+ * library-owned object holding the settings of a coloring + recoloring run
+ * (strategy, X, permutation, iteration count) and the scheduling knobs to run
+ * it with.  gc_plan_color_recolor applies the plan's knobs to that call alone
+ * (on the calling thread), so plans tuned for different graph shapes can run
+ * side by side on several threads while the process-wide knobs stay as they
+ * are.  The graph is not kept: a plan runs on any graph, and results never
+ * depend on the knobs, only the speed does.  A plan may be used by several
+ * threads at once; free it once no call using it is running.
+ */
+typedef struct gc_plan gc_plan;
+
+typedef struct {
+    gc_tuning tuning;    /* the knobs the plan runs with */
+    int32_t strategy;    /* gc_strategy */
+    int32_t X;           /* 1 for First Fit */
+    int32_t perm;        /* gc_perm code (schedule codes included) */
+    int32_t iterations;  /* recoloring iterations */
+    float tuned_ms;      /* time of one run at the tuned knobs (0: not tuned) */
+    int64_t tuned_n;     /* shape of the graph tuned on (0: not tuned) */
+    int64_t tuned_nnz;
+} gc_plan_info;
+
+/* Tunes the knobs for these settings on the caller's graph (gc_autotune, from
+ * the calling thread's knobs) and returns a new plan holding them in *out.
+ * Errors as gc_autotune; *out is untouched on error. */
+gc_status gc_plan_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64_t seed,
+                           gc_perm perm, int32_t iterations, int32_t repeats, gc_plan** out,
+                           void* stream);
+/* A plan from given knobs (NULL: the defaults), e.g. knobs cached from an
+ * earlier tuning.  GC_ERR_INVALID_ARG for knobs gc_set_tuning would reject,
+ * an unknown strategy or permutation, X < 1 for Random-X Fit, iterations < 0
+ * or out == NULL; GC_ERR_OOM if the host allocation fails.  Host only. */
+gc_status gc_plan_create(const gc_tuning* t, gc_strategy strategy, int32_t X, gc_perm perm,
+                         int32_t iterations, gc_plan** out);
+/* Copies a plan's settings and knobs into *out (host only). */
+gc_status gc_plan_get_info(const gc_plan* p, gc_plan_info* out);
+/* gc_color_recolor with the plan's settings, run with the plan's knobs: the
+ * arguments and results are those of gc_color_recolor; `seed` seeds the
+ * random total order and the Random-X Fit draws, `perm_seed` the RAND
+ * permutations. */
+gc_status gc_plan_color_recolor(const gc_plan* p, const gc_graph* g, uint64_t seed,
+                                uint64_t perm_seed, int32_t* colors_out, int32_t* ncolors_per_iter,
+                                gc_stats* stats, gc_validation* check, void* stream);
+/* Releases a plan (NULL is a no-op). */
+void gc_plan_free(gc_plan* p);
 
 /* Testing aid (host-side fault injection; not in the paper): the scratch
  * allocation after the next `after` ones fails once, so the call making it
@@ -441,7 +492,6 @@ void gc_profile_enable(int32_t on);
  * returns how many there are. */
 int32_t gc_profile_read(gc_kernel_time* out, int32_t max);
 
-/* Static description of a status code. */
 /* The strategy, X, permutation and iteration count of a preset (host only;
  * any pointer may be NULL).  GC_ERR_INVALID_ARG for an unknown preset. */
 gc_status gc_preset_params(gc_preset preset, int32_t* strategy, int32_t* X, int32_t* perm,

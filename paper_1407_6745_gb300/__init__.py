@@ -84,6 +84,13 @@ class _Tuning(ctypes.Structure):
                                                "g2_max_deg")]
 
 
+class _PlanInfo(ctypes.Structure):
+    _fields_ = [("tuning", _Tuning), ("strategy", ctypes.c_int32), ("X", ctypes.c_int32),
+                ("perm", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("tuned_ms", ctypes.c_float), ("tuned_n", ctypes.c_int64),
+                ("tuned_nnz", ctypes.c_int64)]
+
+
 class _Request(ctypes.Structure):
     _fields_ = [("graph", _Graph), ("strategy", ctypes.c_int32), ("X", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("perm", ctypes.c_int32), ("iterations", ctypes.c_int32),
@@ -160,6 +167,23 @@ def load():
         lib.gc_preset_params.restype = ctypes.c_int
         lib.gc_server_destroy.argtypes = [H]
         lib.gc_server_destroy.restype = None
+        T = ctypes.POINTER(_Tuning)
+        lib.gc_autotune.argtypes = [G, ctypes.c_int, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int,
+                                    ctypes.c_int32, ctypes.c_int32, T,
+                                    ctypes.POINTER(ctypes.c_float), P]
+        lib.gc_plan_create.argtypes = [T, ctypes.c_int, ctypes.c_int32, ctypes.c_int, ctypes.c_int32,
+                                       ctypes.POINTER(H)]
+        lib.gc_plan_autotune.argtypes = [G, ctypes.c_int, ctypes.c_int32, ctypes.c_uint64,
+                                         ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(H), P]
+        lib.gc_plan_get_info.argtypes = [H, ctypes.POINTER(_PlanInfo)]
+        lib.gc_plan_color_recolor.argtypes = [H, G, ctypes.c_uint64, ctypes.c_uint64, P, P, S,
+                                              ctypes.POINTER(_Validation), P]
+        for f in ("gc_autotune", "gc_plan_create", "gc_plan_autotune", "gc_plan_get_info",
+                  "gc_plan_color_recolor"):
+            getattr(lib, f).restype = ctypes.c_int
+        lib.gc_plan_free.argtypes = [H]
+        lib.gc_plan_free.restype = None
         for f in ("gc_color", "gc_recolor", "gc_color_recolor", "gc_validate", "gc_validate_noalloc",
                   "gc_check_graph", "gc_priorities", "gc_set_tuning", "gc_get_tuning",
                   "gc_server_create", "gc_server_submit", "gc_server_poll", "gc_server_wait",
@@ -552,6 +576,102 @@ def gc_server_destroy(server: GCServer):
         load().gc_server_destroy(server.handle)
         server.handle = None
         server.pending.clear()
+
+
+class GCPlan:
+    """Handle of a gc_plan: run settings plus the knobs to run them with.
+    Use gc_plan_color_recolor / gc_plan_get_info; freed by gc_plan_free, at
+    the end of a ``with`` block, or when the handle is collected."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        gc_plan_free(self)
+
+    def __del__(self):
+        try:
+            gc_plan_free(self)
+        except Exception:
+            pass
+
+
+def _tuning_struct(knobs):
+    t = _Tuning()
+    _check(load().gc_get_tuning(ctypes.byref(t)), "gc_get_tuning")
+    for k, v in (knobs or {}).items():
+        setattr(t, k, int(v))
+    return t
+
+
+def gc_plan_create(tuning=None, strategy="FF", X: int = 1, perm="RV", iterations: int = 0) -> GCPlan:
+    """A plan from knobs (dict of gc_tuning fields over the knobs in force;
+    None: the library defaults) and run settings."""
+    lib = load()
+    h = ctypes.c_void_p()
+    t = _tuning_struct(tuning) if tuning is not None else None
+    _check(lib.gc_plan_create(ctypes.byref(t) if t is not None else None, _strategy(strategy),
+                              int(X), _perm(perm), int(iterations), ctypes.byref(h)),
+           "gc_plan_create")
+    return GCPlan(h)
+
+
+def gc_plan_autotune(offsets, idx, strategy="FF", X: int = 1, seed: int = 0, perm="RV",
+                     iterations: int = 0, repeats: int = 2, stream=None) -> GCPlan:
+    """Tune the knobs for these settings on this graph (device tensors) and
+    return a plan holding them."""
+    lib = load()
+    g, keep = _graph(offsets, idx)
+    h = ctypes.c_void_p()
+    _check(lib.gc_plan_autotune(ctypes.byref(g), _strategy(strategy), int(X),
+                                int(seed) & (2**64 - 1), _perm(perm), int(iterations),
+                                int(repeats), ctypes.byref(h), _stream(keep[0].device, stream)),
+           "gc_plan_autotune")
+    return GCPlan(h)
+
+
+def gc_plan_get_info(plan: GCPlan):
+    """The plan's knobs (dict), settings and tuned time / shape."""
+    info = _PlanInfo()
+    _check(load().gc_plan_get_info(plan.handle, ctypes.byref(info)), "gc_plan_get_info")
+    d = {k: getattr(info, k) for k, _ in _PlanInfo._fields_ if k != "tuning"}
+    d["tuning"] = {k: getattr(info.tuning, k) for k, _ in _Tuning._fields_}
+    return d
+
+
+def gc_plan_color_recolor(plan: GCPlan, offsets, idx, seed: int = 0, perm_seed: int = 0, out=None,
+                          validate: bool = False, stream=None):
+    """gc_color_recolor with the plan's settings and knobs.  Returns (colors,
+    ncolors list, stats dict, validation dict or None)."""
+    lib = load()
+    if not plan.handle:
+        raise ValueError("plan was freed")
+    info = _PlanInfo()
+    _check(lib.gc_plan_get_info(plan.handle, ctypes.byref(info)), "gc_plan_get_info")
+    g, keep = _graph(offsets, idx)
+    dev = keep[0].device
+    if out is None:
+        out = torch.empty(g.n, dtype=torch.int32, device=dev)
+    _check_colors(out, g.n, dev, "out")
+    nc = (ctypes.c_int32 * (info.iterations + 1))()
+    st = _Stats()
+    val = _Validation() if validate else None
+    _check(lib.gc_plan_color_recolor(plan.handle, ctypes.byref(g), int(seed) & (2**64 - 1),
+                                     int(perm_seed) & (2**64 - 1), _ptr(out), nc, ctypes.byref(st),
+                                     ctypes.byref(val) if validate else None, _stream(dev, stream)),
+           "gc_plan_color_recolor")
+    vd = {k: getattr(val, k) for k, _ in _Validation._fields_} if validate else None
+    return out, list(nc), _stats_dict(st), vd
+
+
+def gc_plan_free(plan: GCPlan):
+    """Release the plan (idempotent)."""
+    if plan.handle:
+        load().gc_plan_free(plan.handle)
+        plan.handle = None
 
 
 def gc_set_tuning(**knobs):

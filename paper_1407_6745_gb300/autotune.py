@@ -4,8 +4,9 @@
 descent over the knobs, timing the real pipeline on the device) for the
 fastest knobs and stores them in a JSON cache keyed by the graph's size and
 log2-degree histogram, the strategy and the recoloring settings;
-`apply(...)` looks the key up (tuning if missing) and sets the knobs.  The
-knobs never change results, only speed.
+`apply(...)` looks the key up (tuning if missing) and sets the knobs
+process-wide; `plan(...)` returns them in a plan instead, which applies them
+to its own calls only.  The knobs never change results, only speed.
 """
 from __future__ import annotations
 
@@ -17,7 +18,8 @@ import threading
 
 import torch
 
-from . import _Tuning, _check, _graph, _perm, _stream, _strategy, gc_set_tuning, load
+from . import (_Tuning, _check, _graph, _perm, _stream, _strategy, gc_plan_create,
+                gc_set_tuning, load)
 
 _lock = threading.Lock()
 
@@ -59,11 +61,6 @@ def autotune(offsets, idx, strategy="FF", X: int = 1, seed: int = 0, perm="RV",
              iterations: int = 0, repeats: int = 2, stream=None):
     """Fastest knobs for this graph and these settings: (dict, ms per call)."""
     lib = load()
-    lib.gc_autotune.argtypes = [ctypes.POINTER(type(_graph(offsets, idx)[0])), ctypes.c_int,
-                                ctypes.c_int32, ctypes.c_uint64, ctypes.c_int, ctypes.c_int32,
-                                ctypes.c_int32, ctypes.POINTER(_Tuning),
-                                ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]
-    lib.gc_autotune.restype = ctypes.c_int
     g, keep = _graph(offsets, idx)
     best = _Tuning()
     ms = ctypes.c_float(0.0)
@@ -73,10 +70,7 @@ def autotune(offsets, idx, strategy="FF", X: int = 1, seed: int = 0, perm="RV",
     return {k: getattr(best, k) for k, _ in _Tuning._fields_}, float(ms.value)
 
 
-def apply(offsets, idx, strategy="FF", X: int = 1, seed: int = 0, perm="RV", iterations: int = 0,
-          retune: bool = False):
-    """Sets the cached knobs for this graph shape (tuning and caching them on
-    a miss); returns them."""
+def _cached(offsets, idx, strategy, X, seed, perm, iterations, retune):
     key = shape_key(offsets, strategy, X, perm, iterations)
     with _lock:
         cache = _load_cache()
@@ -86,5 +80,22 @@ def apply(offsets, idx, strategy="FF", X: int = 1, seed: int = 0, perm="RV", ite
             entry = {"knobs": knobs, "ms": ms}
             cache[key] = entry
             _store_cache(cache)
-    gc_set_tuning(**entry["knobs"])
     return entry["knobs"]
+
+
+def apply(offsets, idx, strategy="FF", X: int = 1, seed: int = 0, perm="RV", iterations: int = 0,
+          retune: bool = False):
+    """Sets the cached knobs for this graph shape process-wide (tuning and
+    caching them on a miss); returns them."""
+    knobs = _cached(offsets, idx, strategy, X, seed, perm, iterations, retune)
+    gc_set_tuning(**knobs)
+    return knobs
+
+
+def plan(offsets, idx, strategy="FF", X: int = 1, seed: int = 0, perm="RV", iterations: int = 0,
+         retune: bool = False):
+    """A plan (gc_plan_create) holding the cached knobs for this graph shape
+    and these settings, tuning and caching them on a miss; the process-wide
+    knobs are left alone."""
+    knobs = _cached(offsets, idx, strategy, X, seed, perm, iterations, retune)
+    return gc_plan_create(knobs, strategy, X, perm, iterations)

@@ -4,6 +4,7 @@
 #include <climits>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "gc_internal.h"
@@ -196,6 +197,11 @@ thread_local Tuning t_tune;
 void set_thread_tuning(const Tuning* t) {
     t_tune_set = t != nullptr;
     if (t) t_tune = *t;
+}
+
+bool thread_tuning(Tuning* out) {
+    if (t_tune_set && out) *out = t_tune;
+    return t_tune_set;
 }
 
 Tuning current_tuning() {
@@ -602,7 +608,7 @@ gc_status gc_validate_noalloc(const gc_graph* g, const int32_t* colors, gc_valid
     return validate_noalloc_device(dg, colors, out, static_cast<cudaStream_t>(stream));
 }
 
-gc_status gc_set_tuning(const gc_tuning* t) {
+static gc_status tuning_from(const gc_tuning* t, Tuning* out) {
     Tuning v = default_tuning();
     if (t) {
         if (t->g2_max_deg < 0 || t->g4_max_deg < t->g2_max_deg || t->g8_max_deg < t->g4_max_deg || t->g16_max_deg < t->g8_max_deg ||
@@ -621,6 +627,29 @@ gc_status gc_set_tuning(const gc_tuning* t) {
         v.rc_warp_max_deg = t->rc_warp_max_deg;
         v.g2_max_deg = t->g2_max_deg;
     }
+    *out = v;
+    return GC_OK;
+}
+
+static gc_tuning tuning_to(const Tuning& t) {
+    gc_tuning out;
+    out.g4_max_deg = t.g4_max_deg;
+    out.g8_max_deg = t.g8_max_deg;
+    out.g16_max_deg = t.g16_max_deg;
+    out.warp_max_deg = t.warp_max_deg;
+    out.grid_blocks = t.grid_blocks;
+    out.recolor_mode = t.recolor_mode;
+    out.spin_limit = t.spin_limit;
+    out.spec_graph = t.spec_graph;
+    out.rc_warp_max_deg = t.rc_warp_max_deg;
+    out.g2_max_deg = t.g2_max_deg;
+    return out;
+}
+
+gc_status gc_set_tuning(const gc_tuning* t) {
+    Tuning v;
+    gc_status st = tuning_from(t, &v);
+    if (st != GC_OK) return st;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune = v;
     return GC_OK;
@@ -628,17 +657,7 @@ gc_status gc_set_tuning(const gc_tuning* t) {
 
 gc_status gc_get_tuning(gc_tuning* out) {
     if (!out) return GC_ERR_INVALID_ARG;
-    const Tuning t = current_tuning();
-    out->g4_max_deg = t.g4_max_deg;
-    out->g8_max_deg = t.g8_max_deg;
-    out->g16_max_deg = t.g16_max_deg;
-    out->warp_max_deg = t.warp_max_deg;
-    out->grid_blocks = t.grid_blocks;
-    out->recolor_mode = t.recolor_mode;
-    out->spin_limit = t.spin_limit;
-    out->spec_graph = t.spec_graph;
-    out->rc_warp_max_deg = t.rc_warp_max_deg;
-    out->g2_max_deg = t.g2_max_deg;
+    *out = tuning_to(current_tuning());
     return GC_OK;
 }
 
@@ -649,8 +668,7 @@ gc_status gc_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64
     if (st != GC_OK) return st;
     if (!best || g->mem != GC_MEM_DEVICE || repeats < 1 || g->n < 1) return GC_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    gc_tuning orig;
-    gc_get_tuning(&orig);
+    const gc_tuning orig = tuning_to(current_tuning());
     int32_t* colors = nullptr;
     Scratch sc;
     if (!sc.alloc(g->n * sizeof(int32_t), s)) return GC_ERR_OOM;
@@ -658,9 +676,12 @@ gc_status gc_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    // each candidate runs on this thread only (the process-wide knobs stay)
     auto time_it = [&](const gc_tuning& t, float* ms) -> gc_status {
-        gc_status r = gc_set_tuning(&t);
+        Tuning v;
+        gc_status r = tuning_from(&t, &v);
         if (r != GC_OK) return r;
+        ThreadTuningScope scope(v);
         r = gc_color_recolor_impl(g, strategy, X, seed, perm, iterations, 0, colors, nullptr, nullptr,
                                   nullptr, stream);  // warm-up
         if (r != GC_OK) return r;
@@ -706,7 +727,6 @@ gc_status gc_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64
             if (st == GC_OK && ms < cur_ms) { cur = t; cur_ms = ms; }
         }
     }
-    gc_set_tuning(&orig);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != GC_OK) return st;
@@ -714,6 +734,77 @@ gc_status gc_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64
     if (best_ms) *best_ms = cur_ms;
     return GC_OK;
 }
+
+}  // extern "C"
+
+// A plan: run settings plus the knobs to run them with (see gc.h).
+struct gc_plan {
+    Tuning tune;
+    gc_plan_info info;
+};
+
+extern "C" {
+
+gc_status gc_plan_create(const gc_tuning* t, gc_strategy strategy, int32_t X, gc_perm perm,
+                         int32_t iterations, gc_plan** out) {
+    if (!out) return GC_ERR_INVALID_ARG;
+    Tuning v;
+    if (tuning_from(t, &v) != GC_OK) return GC_ERR_INVALID_ARG;
+    if (strategy != GC_FIRST_FIT && strategy != GC_RANDOM_X_FIT) return GC_ERR_INVALID_ARG;
+    if (strategy == GC_FIRST_FIT) X = 1;
+    if (X < 1 || !perm_valid(perm) || iterations < 0) return GC_ERR_INVALID_ARG;
+    gc_plan* p = new (std::nothrow) gc_plan;
+    if (!p) return GC_ERR_OOM;
+    p->tune = v;
+    std::memset(&p->info, 0, sizeof(p->info));
+    p->info.tuning = tuning_to(v);
+    p->info.strategy = strategy;
+    p->info.X = X;
+    p->info.perm = perm;
+    p->info.iterations = iterations;
+    *out = p;
+    return GC_OK;
+}
+
+gc_status gc_plan_autotune(const gc_graph* g, gc_strategy strategy, int32_t X, uint64_t seed,
+                           gc_perm perm, int32_t iterations, int32_t repeats, gc_plan** out,
+                           void* stream) {
+    if (!out) return GC_ERR_INVALID_ARG;
+    gc_tuning best;
+    float ms = 0.f;
+    gc_status st = gc_autotune(g, strategy, X, seed, perm, iterations, repeats, &best, &ms, stream);
+    if (st != GC_OK) return st;
+    gc_plan* p = nullptr;
+    if ((st = gc_plan_create(&best, strategy, X, perm, iterations, &p)) != GC_OK) return st;
+    p->info.tuned_ms = ms;
+    p->info.tuned_n = g->n;
+    p->info.tuned_nnz = g->nnz;
+    *out = p;
+    return GC_OK;
+}
+
+gc_status gc_plan_get_info(const gc_plan* p, gc_plan_info* out) {
+    if (!p || !out) return GC_ERR_INVALID_ARG;
+    *out = p->info;
+    return GC_OK;
+}
+
+gc_status gc_plan_color_recolor(const gc_plan* p, const gc_graph* g, uint64_t seed,
+                                uint64_t perm_seed, int32_t* colors_out, int32_t* ncolors_per_iter,
+                                gc_stats* stats, gc_validation* check, void* stream) {
+    if (!p) return GC_ERR_INVALID_ARG;
+    gc_status st;
+    {
+        ThreadTuningScope scope(p->tune);
+        st = gc_color_recolor_impl(g, static_cast<gc_strategy>(p->info.strategy), p->info.X, seed,
+                                   static_cast<gc_perm>(p->info.perm), p->info.iterations, perm_seed,
+                                   colors_out, ncolors_per_iter, stats, check, stream);
+    }
+    prof_collect();
+    return st;
+}
+
+void gc_plan_free(gc_plan* p) { delete p; }
 
 gc_status gc_preset_params(gc_preset preset, int32_t* strategy, int32_t* X, int32_t* perm,
                            int32_t* iterations) {

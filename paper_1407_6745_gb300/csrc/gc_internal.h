@@ -62,6 +62,22 @@ void prof_collect();
 Tuning current_tuning();
 // Gives the calling thread its own tuning (nullptr: back to the process-wide one).
 void set_thread_tuning(const Tuning* t);
+// The calling thread's own tuning, if it has one (false: none).
+bool thread_tuning(Tuning* out);
+
+// Gives the calling thread a tuning for the scope's lifetime, then puts back
+// what the thread had before.
+struct ThreadTuningScope {
+    bool had;
+    Tuning prev;
+    explicit ThreadTuningScope(const Tuning& t) {
+        had = thread_tuning(&prev);
+        set_thread_tuning(&t);
+    }
+    ThreadTuningScope(const ThreadTuningScope&) = delete;
+    ThreadTuningScope& operator=(const ThreadTuningScope&) = delete;
+    ~ThreadTuningScope() { set_thread_tuning(had ? &prev : nullptr); }
+};
 
 gc_status cuda_status(cudaError_t e);
 gc_status status_from_err_bits(uint32_t bits);

@@ -94,3 +94,29 @@ def test_schedule_codes_match_the_oracle():
     import paper_1407_6745_gb300 as gc
     for name in ("RV", "NI", "ND", "RAND", "ND-RAND%5", "ND-RAND%10", "ND-RAND%2^i", "ND-RAND%1"):
         assert gc._perm(name) == oracle.perm_code(name)
+
+
+def test_plans_are_host_objects():
+    """gc_plan_create checks its arguments and keeps its settings and knobs
+    without touching the GPU or the process-wide knobs."""
+    import paper_1407_6745_gb300 as gc
+    assert ctypes.sizeof(gc._PlanInfo) == 40 + 4 * 4 + 4 + 4 + 2 * 8  # float padded before int64
+    gc.gc_set_tuning()
+    before = gc.gc_get_tuning()
+    with gc.gc_plan_create({"g4_max_deg": 8, "g8_max_deg": 16, "g16_max_deg": 32, "g2_max_deg": 4},
+                           "RXF", 6, "ND-RAND%2^i", 9) as p:
+        info = gc.gc_plan_get_info(p)
+        assert info["strategy"] == gc.RANDOM_X_FIT and info["X"] == 6 and info["iterations"] == 9
+        assert info["perm"] == gc._perm("ND-RAND%2^i")
+        assert info["tuning"] == dict(before, g4_max_deg=8, g8_max_deg=16, g16_max_deg=32, g2_max_deg=4)
+        assert info["tuned_ms"] == 0 and info["tuned_n"] == 0 and info["tuned_nnz"] == 0
+    assert p.handle is None and gc.gc_get_tuning() == before
+    with gc.gc_plan_create(None, "FF", 17, "RV", 0) as p:  # First Fit ignores X
+        info = gc.gc_plan_get_info(p)
+        assert info["X"] == 1 and info["tuning"] == before
+    bad = [dict(tuning={"g4_max_deg": 65, "g8_max_deg": 64}), dict(strategy=5), dict(strategy="RXF", X=0),
+           dict(perm=7), dict(iterations=-1), dict(tuning={"spin_limit": 0})]
+    for kw in bad:
+        with pytest.raises(gc.GCError) as e:
+            gc.gc_plan_create(**kw)
+        assert e.value.name == "GC_ERR_INVALID_ARG", kw
