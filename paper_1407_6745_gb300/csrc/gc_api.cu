@@ -137,7 +137,7 @@ const char* const kKernelNames[] = {
     "k_rc_bucket", "k_rc_validate", "k_rc_hist", "k_rc_order", "k_rc_scatter",
     "k_rc_recolor_coop", "k_rc_recolor_step", "k_validate", "k_validate_heavy",
     "k_mark_present", "k_count_bits", "k_check_graph", "spec_rounds_graph", "k_batch", "k_brc_hist",
-    "k_brc_order", "k_brc_segments"};
+    "k_brc_order", "k_brc_segments", "k_mark_colors"};
 static_assert(sizeof(kKernelNames) / sizeof(kKernelNames[0]) == KID_COUNT_,
               "one name per KernelId");
 std::atomic<bool> g_prof_on{false};

@@ -42,7 +42,7 @@ enum KernelId {
     KID_RC_BUCKET, KID_RC_VALIDATE, KID_RC_HIST, KID_RC_ORDER, KID_RC_SCATTER,
     KID_RC_RECOLOR, KID_RC_STEP, KID_VALIDATE, KID_VALIDATE_HEAVY, KID_MARK_PRESENT,
     KID_COUNT_BITS, KID_CHECK_GRAPH, KID_SPEC_GRAPH, KID_BATCH, KID_BRC_HIST, KID_BRC_ORDER,
-    KID_BRC_SEGMENTS, KID_COUNT_
+    KID_BRC_SEGMENTS, KID_MARK, KID_COUNT_
 };
 void prof_begin(KernelId k, cudaStream_t s);
 void prof_end(KernelId k, cudaStream_t s);
