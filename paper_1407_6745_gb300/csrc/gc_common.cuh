@@ -378,26 +378,25 @@ __device__ __forceinline__ void for_each_nbr(const Graph& g, int64_t beg, int32_
 
 // Colors of the neighbors through a Fetch: raw(u) issues the load (no
 // branch), resolve(u, x) turns it into a color, or a value < 1 to ignore.
-template <int UC, class Fetch, class Mark>
+template <int UC, class Fetch, class Mark, bool kVec = false>
 __device__ __forceinline__ void scan_row(const Graph& g, int64_t beg, int32_t deg, int32_t lane0,
                                          int32_t stride, const Fetch& fetch, Mark&& mark,
                                          uint32_t* err) {
-    for_each_nbr<UC, int32_t, false>(
+    for_each_nbr<UC, int32_t, kVec>(
         g, beg, deg, lane0, stride, [&](int32_t u) { return fetch.raw(u); },
         [&](int32_t u, int32_t x) { mark(fetch.resolve(u, x)); }, err);
 }
 
 // Register path, G lanes per vertex; requires deg + j < 64.  All 32 lanes of
 // the warp must call it (lanes without a vertex pass deg = 0).
-template <int G, int U, class Fetch>
+template <int G, int U, class Fetch, bool kVec = false>
 __device__ __forceinline__ int32_t choose_reg(const Graph& g, int64_t beg, int32_t deg, int gl,
                                               uint32_t j, const Fetch& fetch, uint32_t* err) {
     uint64_t m = 0;
-    scan_row<U>(g, beg, deg, gl, G, fetch,
-                [&](int32_t c) {
-                    if (static_cast<uint32_t>(c - 1) < 64u) m |= 1ull << (c - 1);
-                },
-                err);
+    auto mark = [&](int32_t c) {
+        if (static_cast<uint32_t>(c - 1) < 64u) m |= 1ull << (c - 1);
+    };
+    scan_row<U, Fetch, decltype(mark)&, kVec>(g, beg, deg, gl, G, fetch, mark, err);
     m = group_or<G>(m);
     const uint64_t free_bits = ~m;
     if (j == 0) return __ffsll(static_cast<long long>(free_bits));
