@@ -371,7 +371,7 @@ gc_status gc_check_graph(const gc_graph* g, int64_t* first_bad_vertex, void* str
  * else 32; otherwise by one warp with a shared-memory bitmap if
  * d <= warp_max_deg, else by a whole block (coloring) or split into chunks
  * of 256 neighbors (recoloring, where rc_warp_max_deg takes the place of
- * warp_max_deg).  grid_blocks = 0 sizes every
+ * warp_max_deg and rc_g2_max_deg, capped at g4_max_deg, that of g2_max_deg).  grid_blocks = 0 sizes every
  * grid to the blocks that fit on the GPU at once.  recolor_mode 0 runs each recoloring iteration as one dataflow
  * launch (vertices wait, with a bounded spin of spin_limit polls, for their
  * earlier-class neighbors); 1 launches one grid per color class.
@@ -392,6 +392,7 @@ typedef struct {
     int32_t spec_graph;
     int32_t rc_warp_max_deg;
     int32_t g2_max_deg;
+    int32_t rc_g2_max_deg;
 } gc_tuning;
 
 /* Sets the scheduling knobs (NULL restores the defaults).  GC_ERR_INVALID_ARG
@@ -404,7 +405,8 @@ gc_status gc_get_tuning(gc_tuning* out);
  * Autotuner: times gc_color_recolor on the caller's graph (device memory) for
  * candidate scheduling knobs, by coordinate descent from the knobs in force
  * for the calling thread (lane-group thresholds, warp_max_deg,
- * rc_warp_max_deg, g2_max_deg, recolor_mode, spec_graph, grid size),
+ * rc_warp_max_deg, g2_max_deg, rc_g2_max_deg, recolor_mode, spec_graph,
+ * grid size),
  * `repeats` timed runs each after one warm-up, and returns the fastest in
  * `best` with its time.  Results are identical for every candidate, so only
  * speed is compared.  The candidates are applied to the calling thread only:

@@ -81,7 +81,7 @@ class _Tuning(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in ("g4_max_deg", "g8_max_deg", "g16_max_deg",
                                                "warp_max_deg", "grid_blocks", "recolor_mode",
                                                "spin_limit", "spec_graph", "rc_warp_max_deg",
-                                               "g2_max_deg")]
+                                               "g2_max_deg", "rc_g2_max_deg")]
 
 
 class _PlanInfo(ctypes.Structure):

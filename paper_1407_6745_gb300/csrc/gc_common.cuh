@@ -48,11 +48,13 @@ struct Tuning {
     int32_t spec_graph;    // 1: speculative rounds in a CUDA graph WHILE node; 0: host loop
     int32_t rc_warp_max_deg;  // warp_max_deg of the recoloring phase
     int32_t g2_max_deg;    // deg <= this -> 2 lanes (0: none)
+    int32_t rc_g2_max_deg;  // g2_max_deg of the recoloring phase (capped at g4_max_deg)
 };
 
-// The recoloring phase's view of the knobs: its own warp threshold.
+// The recoloring phase's view of the knobs: its own warp and 2-lane thresholds.
 __host__ __device__ inline Tuning recolor_tuning(Tuning t) {
     t.warp_max_deg = t.rc_warp_max_deg;
+    t.g2_max_deg = t.rc_g2_max_deg < t.g4_max_deg ? t.rc_g2_max_deg : t.g4_max_deg;
     return t;
 }
 

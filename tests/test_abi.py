@@ -58,7 +58,12 @@ def test_argument_checks_need_no_gpu():
     with pytest.raises(gc.GCError):
         gc.gc_set_tuning(g4_max_deg=9, g8_max_deg=8)
     gc.gc_set_tuning()
-    assert gc.gc_get_tuning()["warp_max_deg"] == 1024 and gc.gc_get_tuning()["rc_warp_max_deg"] == 512
+    t = gc.gc_get_tuning()
+    assert t["warp_max_deg"] == 1024 and t["rc_warp_max_deg"] == 512
+    assert t["g2_max_deg"] == 32 and t["rc_g2_max_deg"] == 16
+    with pytest.raises(gc.GCError):
+        gc.gc_set_tuning(rc_g2_max_deg=-1)
+    gc.gc_set_tuning()
     for budget, max_batch, workers in ((0, 8, 2), (1 << 20, 0, 2), (1 << 20, 70000, 2), (1 << 20, 8, 0)):
         with pytest.raises(gc.GCError) as e:
             gc.gc_server_create(budget, max_batch, workers)
@@ -100,7 +105,9 @@ def test_plans_are_host_objects():
     """gc_plan_create checks its arguments and keeps its settings and knobs
     without touching the GPU or the process-wide knobs."""
     import paper_1407_6745_gb300 as gc
-    assert ctypes.sizeof(gc._PlanInfo) == 40 + 4 * 4 + 4 + 4 + 2 * 8  # float padded before int64
+    tun = ctypes.sizeof(gc._Tuning)
+    assert tun == 4 * len(gc._Tuning._fields_)
+    assert ctypes.sizeof(gc._PlanInfo) == (tun + 4 * 4 + 4 + 7) // 8 * 8 + 2 * 8  # int64 aligned
     gc.gc_set_tuning()
     before = gc.gc_get_tuning()
     with gc.gc_plan_create({"g4_max_deg": 8, "g8_max_deg": 16, "g16_max_deg": 32, "g2_max_deg": 4},

@@ -179,6 +179,9 @@ def test_complete_graph_crosses_register_window():
     dict(g2_max_deg=4, recolor_mode=1),
     dict(rc_warp_max_deg=0),
     dict(rc_warp_max_deg=1 << 30),
+    dict(rc_g2_max_deg=0),
+    dict(rc_g2_max_deg=64, g2_max_deg=0),
+    dict(g2_max_deg=16, rc_g2_max_deg=32),
 ])
 def test_results_do_not_depend_on_scheduling(knobs):
     g = gg.hubs(THRESHOLD_DEGREES[:-1], 6000, seed=8)
