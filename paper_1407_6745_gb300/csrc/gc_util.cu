@@ -21,7 +21,7 @@ struct ValCtrl {
     int32_t big_colors;     // vertices with a color >= kPresColors
 };
 
-constexpr int kValG = 8;                 // lanes per light row
+constexpr int kValG = 4;                 // lanes per light row (measured: 8 -> 4 saves 30 us on the stencil)
 constexpr int32_t kHeavyDeg = 256;       // heavier rows: one block each
 constexpr int kPresWords = 2048;         // presence bitmap of colors < 65536
 constexpr int32_t kPresColors = kPresWords * 32;
