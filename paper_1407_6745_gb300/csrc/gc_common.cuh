@@ -18,8 +18,8 @@ namespace gc {
 constexpr int kBlock = 256;          // threads per block, every kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kNB = 7;               // degree buckets
-// bucket b: 0 block/vertex, 1 warp/vertex + smem bitmap, 2..5 group of
-// 32/16/8/4 lanes per vertex with a 64-bit register mask
+// bucket b: 0 block/vertex, 1 warp/vertex + smem bitmap, 2..6 group of
+// 32/16/8/4/2 lanes per vertex with a 64-bit register mask
 __host__ __device__ constexpr int bucket_group(int b) {
     return b == 0 ? kBlock : b == 1 ? 32 : b == 2 ? 32 : b == 3 ? 16 : b == 4 ? 8 : b == 5 ? 4 : 2;
 }
@@ -28,7 +28,6 @@ __host__ __device__ constexpr int bucket_tile(int b) {
     return b == 0 ? 1 : kBlock / bucket_group(b);
 }
 constexpr int kWarpBitmapWords = 64;    // 2048 colors per window, per warp
-constexpr int kBlockBitmapWords = 4096; // 131072 colors per window, per block
 
 // error bits accumulated on the device
 constexpr uint32_t kErrBadGraph = 1u;
@@ -449,70 +448,8 @@ __device__ __forceinline__ int32_t choose_warp(const Graph& g, int64_t beg, int3
     }
 }
 
-struct BlockScratch {
-    uint32_t bm[kBlockBitmapWords];
-    uint32_t wsum[kWarps];
-    int32_t result;
-};
-
-// Block path: the whole block on one vertex, bitmap of 131072 colors per
-// window.  Every thread of the block must call it.
-template <int U, class Fetch>
-__device__ __forceinline__ int32_t choose_block(const Graph& g, int64_t beg, int32_t deg,
-                                                uint32_t j, const Fetch& fetch, BlockScratch& s,
-                                                uint32_t* err) {
-    constexpr int kPer = kBlockBitmapWords / kBlock;
-    const int t = threadIdx.x, l = lane_id(), w = t >> 5;
-    int32_t base = 1;
-    for (;;) {
-        for (int i = t; i < kBlockBitmapWords; i += kBlock) s.bm[i] = 0u;
-        __syncthreads();
-        scan_row<1>(g, beg, deg, t, kBlock, fetch,
-                    [&](int32_t c) {
-                        const uint32_t d = static_cast<uint32_t>(c - base);
-                        if (c > 0 && d < 32u * kBlockBitmapWords) atomicOr(&s.bm[d >> 5], 1u << (d & 31));
-                    },
-                    err);
-        __syncthreads();
-        uint32_t cnt = 0;
-#pragma unroll
-        for (int i = 0; i < kPer; ++i) cnt += __popc(~s.bm[t * kPer + i]);
-        const uint32_t incl_w = warp_inclusive_scan(cnt);
-        if (l == 31) s.wsum[w] = incl_w;
-        __syncthreads();
-        uint32_t before = 0, total = 0;
-#pragma unroll
-        for (int i = 0; i < kWarps; ++i) {
-            const uint32_t x = s.wsum[i];
-            if (i < w) before += x;
-            total += x;
-        }
-        const uint32_t incl = incl_w + before, excl = incl - cnt;
-        if (j < total) {
-            if (j >= excl && j < incl) {
-                uint32_t jj = j - excl;
-                for (int i = 0; i < kPer; ++i) {
-                    const uint32_t f = ~s.bm[t * kPer + i];
-                    const uint32_t pc = __popc(f);
-                    if (jj < pc) {
-                        s.result = base + 32 * (t * kPer + i) + select_bit32(f, jj);
-                        break;
-                    }
-                    jj -= pc;
-                }
-            }
-            __syncthreads();
-            const int32_t color = s.result;
-            __syncthreads();
-            return color;
-        }
-        j -= total;
-        base += 32 * kBlockBitmapWords;
-        __syncthreads();
-    }
-}
-
-// 4-id pieces per lane per batch, per group size (32/16/8/4 lanes).
+// Single ids per lane per batch in the recoloring scans, in units of 4, per
+// group size (32/16/8/4/2 lanes).
 template <int G> struct LanesUnroll { static constexpr int U = (G == 4 || G == 2) ? 2 : 1; };
 
 // ---------------------------------------------------------------------------
