@@ -117,3 +117,18 @@ def test_plan_errors():
     with pytest.raises(gc.GCError) as e:  # tuning needs the graph on the device
         gc.gc_plan_autotune(g.offsets, g.idx, "FF")
     assert e.value.name == "GC_ERR_INVALID_ARG"
+
+
+def test_cached_plan_reuses_the_tuned_knobs(tmp_path, monkeypatch):
+    from paper_1407_6745_gb300 import autotune
+    monkeypatch.setenv("GC_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    g = gg.workload("rmat10")
+    off, idx = g.offsets.cuda(), g.idx.cuda()
+    before = gc.gc_get_tuning()
+    with autotune.plan(off, idx, "FF", 1, 3, "NI", 2) as p1, \
+            autotune.plan(off, idx, "FF", 1, 3, "NI", 2) as p2:  # the second from the cache
+        assert (tmp_path / "tune.json").exists() and gc.gc_get_tuning() == before
+        assert gc.gc_plan_get_info(p1)["tuning"] == gc.gc_plan_get_info(p2)["tuning"]
+        exp, enc = _expect(g, 1, 3, "NI", 2, 0)
+        r, nc, _, _ = gc.gc_plan_color_recolor(p2, off, idx, 3, 0)
+        assert np.array_equal(r.cpu().numpy(), exp) and nc == enc
