@@ -147,8 +147,10 @@ def test_degree_thresholds(strategy, X):
 
 
 def test_block_bitmap_window():
-    """Random-X draws past the 131072-color block bitmap window (hubs of
-    degree > 2048 go to the block path)."""
+    """Random-X draws far past a heavy row's marked bitmap (about degree + 128
+    colors): its tentative color comes from the full-row fallback, in 2048-color
+    windows, up to colors above 131072 (hubs of degree > 2048 are block-bucket
+    rows)."""
     g = gg.hubs([3000, 5000, 2100], 8000, seed=4)
     c = _spec(g, "RXF", 140000, 5)
     assert c.max() > 131072
