@@ -60,9 +60,9 @@
  * (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
  * SC'11): a 10-round Feistel-like network on four 32-bit words using the two
  * multipliers 0xD2511F53 and 0xCD9E8D57 and the Weyl key increments
- * 0x9E3779B9 and 0xBB67AE85.  Known-answer vectors are not available here,
- * so "this is bit-for-bit the canonical Philox" is parity unpinned; the
- * method's results do not depend on it.
+ * 0x9E3779B9 and 0xBB67AE85.  It is pinned against an independent
+ * implementation, PyTorch's open-source at::Philox4_32 engine, whole blocks
+ * and the three counter layouts below (tests/test_philox_pin.py).
  */
 #include <stdint.h>
 #include <stdlib.h>
