@@ -339,22 +339,28 @@ gc_status gc_validate(const gc_graph* g, const int32_t* colors, gc_validation* o
 
 /*
  * gc_validate that allocates nothing (the paper has no counterpart: this is
- * a library convenience).  For callers that cannot allocate device memory --
- * code running while a stream is being captured into a CUDA graph, a caller
- * whose allocator is locked or exhausted, a latency-critical path that must
- * not wait on the driver's allocator -- the call uses a fixed scratch array
- * of about 8.3 KB in the library's static device memory instead of the pool;
- * every GPU that loads libgc.so holds that array until the process exits.
+ * a library convenience).  For callers that cannot allocate device memory:
+ * a process whose own caching allocator has reserved the device's memory up
+ * front, so that a cudaMalloc would fail or fragment it; a caller checking a
+ * result right after an out-of-memory error; a latency-critical path that
+ * must not wait on the driver's allocator.  The call uses a fixed scratch
+ * array of about 8.3 KB in the library's static device memory instead of the
+ * pool; every GPU that loads libgc.so holds that array until the process
+ * exits.
  *   - Same result as gc_validate; the graph and colors must be device memory
  *     (GC_MEM_HOST is rejected with GC_ERR_INVALID_ARG: staging would allocate).
  *   - Colors must be below 65536: the array's presence bitmap counts distinct
  *     colors up to there; a larger color gives GC_ERR_INVALID_ARG.
+ *   - Like gc_validate it copies its result to the host and synchronizes
+ *     `stream` before returning.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call outside any stream capture.
+ *     (cudaGetSymbolAddress) with that device current.
  *   - All calls share the array, which each call clears before use; calls
  *     that overlap on the GPU (two streams, two host threads) race on it and
  *     must be serialised by the caller.
- *   - It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.  Its
+ *     launches are counted by gc_kernel_launches but not timed by
+ *     gc_profile_enable.
  */
 gc_status gc_validate_noalloc(const gc_graph* g, const int32_t* colors, gc_validation* out,
                               void* stream);

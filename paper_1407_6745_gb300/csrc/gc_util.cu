@@ -62,7 +62,7 @@ __device__ __forceinline__ void flush_presence(const ValArgs& a, uint32_t* s_pre
         if (s_pres[i]) atomicOr(&a.pres[i], s_pres[i]);
 }
 
-// Light rows: 8 lanes per vertex; heavy rows are listed for the next pass.
+// Light rows: kValG lanes per vertex; heavy rows are listed for the next pass.
 __global__ void __launch_bounds__(kBlock) k_validate(ValArgs a) {
     __shared__ uint32_t s_pres[kPresWords];
     for (int i = threadIdx.x; i < kPresWords; i += kBlock) s_pres[i] = 0u;
@@ -198,16 +198,17 @@ gc_status validate_device(const Graph& g, const int32_t* colors, gc_validation* 
 
 // ---------------------------------------------------------------------------
 // Validation without allocation (gc_validate_noalloc).  For callers that
-// must not allocate device memory: code that runs while a CUDA stream is
-// being captured into a graph (where a cudaMalloc would break the capture),
-// a caller whose allocator is locked or already exhausted, or a real-time
-// path that must not stall on the driver's allocator.  Its scratch is a
-// file-scope device array, held by every device that loads the library
-// until the process exits; every call shares it, so two calls that overlap
-// on the GPU (e.g. on two streams) race on it and must be serialised by
-// the caller.  The presence bitmap covers colors below kPresColors (65536);
-// a coloring with a larger color is rejected, since counting its distinct
-// colors would need scratch beyond the array.
+// cannot allocate device memory: a process whose own caching allocator has
+// reserved the device's memory up front (a cudaMalloc would fail or fragment
+// it), a caller checking a result after an out-of-memory error, or a
+// latency-critical path that must not wait on the driver's allocator.  Its
+// scratch is a file-scope device array, held by every device that loads the
+// library until the process exits; every call shares it, so two calls that
+// overlap on the GPU (e.g. on two streams) race on it and must be serialised
+// by the caller.  The call reads its result back and synchronizes the
+// caller's stream.  The presence bitmap covers colors below kPresColors
+// (65536); a coloring with a larger color is rejected, since counting its
+// distinct colors would need scratch beyond the array.
 // ---------------------------------------------------------------------------
 struct NoAllocScratch {
     ValCtrl ctrl;
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kBlock) k_validate_na_clear(NoAllocScratch* sc
         sc->pres[i] = 0u;
 }
 
-// Light rows, 8 lanes per vertex; heavy rows are left to the next kernel
+// Light rows, kValG lanes per vertex; heavy rows are left to the next kernel
 // (which finds them again by degree instead of through a list).
 __global__ void __launch_bounds__(kBlock) k_validate_na_light(ValArgs a) {
     __shared__ uint32_t s_pres[kPresWords];
@@ -360,13 +361,24 @@ gc_status validate_noalloc_device(const Graph& g, const int32_t* colors, gc_vali
     gc_status st = noalloc_scratch(&sc);
     if (st != GC_OK) return st;
     ValArgs a{g, colors, &sc->ctrl, sc->pres, nullptr};
+    // Each launch is checked before the next is enqueued: a clear that failed
+    // to launch must not let the read-back return the previous call's counts.
+    // (Not bracketed by the profiling events, which would create events.)
+    cudaError_t ce;
     k_validate_na_clear<<<8, kBlock, 0, s>>>(sc);
+    note_launches(1);
+    if ((ce = cudaGetLastError()) != cudaSuccess) return cuda_status(ce);
     k_validate_na_light<<<noalloc_grid(reinterpret_cast<const void*>(k_validate_na_light)), kBlock, 0, s>>>(a);
+    note_launches(1);
+    if ((ce = cudaGetLastError()) != cudaSuccess) return cuda_status(ce);
     k_validate_na_heavy<<<noalloc_grid(reinterpret_cast<const void*>(k_validate_na_heavy)), kBlock, 0, s>>>(a);
+    note_launches(1);
+    if ((ce = cudaGetLastError()) != cudaSuccess) return cuda_status(ce);
     k_count_bits<<<8, kBlock, 0, s>>>(kPresWords, sc->pres, &sc->ctrl);
-    note_launches(4);
+    note_launches(1);
+    if ((ce = cudaGetLastError()) != cudaSuccess) return cuda_status(ce);
     ValCtrl h;
-    cudaError_t ce = cudaMemcpyAsync(&h, &sc->ctrl, sizeof(h), cudaMemcpyDeviceToHost, s);
+    ce = cudaMemcpyAsync(&h, &sc->ctrl, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return cuda_status(ce);
     if (h.err & kErrBadGraph) return GC_ERR_BAD_GRAPH;

@@ -1,17 +1,20 @@
 """gc_validate_noalloc: the validation entry point that allocates nothing.
 
-It serves callers that cannot allocate device memory -- e.g. code running
-while a stream is captured into a CUDA graph, or with an exhausted or locked
+It serves callers that cannot allocate device memory -- a process whose own
+caching allocator has reserved the device's memory up front, a check right
+after an out-of-memory error, a path that must not wait on the driver's
 allocator -- by working in a fixed scratch array in the library's static
 device memory.  These checks call it through the C ABI and compare it with
-gc_validate (the allocating entry point) on consecutive calls, so a result
-left in the shared array by one call cannot leak into the next.
+gc_validate (the allocating entry point) and with the CPU oracle's validation
+on consecutive calls, so a result left in the shared array by one call cannot
+leak into the next.
 """
 import numpy as np
 import pytest
 import torch
 
 import graphgen as gg
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -29,6 +32,8 @@ def _both(off, idx, colors):
     got = gc.gc_validate_noalloc(off, idx, colors)
     ref = gc.gc_validate(off, idx, colors)
     assert got == ref
+    want = oracle.validate(off.cpu().numpy(), idx.cpu().numpy(), colors.cpu().numpy())
+    assert got == want
     return got
 
 
