@@ -1,20 +1,27 @@
 """Benchmark: speculative coloring + iterative recoloring on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gc|reference]
-                    [--workload st27-128] [--no-cpu-baseline] [--no-e2e]
+                    [--workload rmat24] [--no-cpu-baseline] [--no-e2e]
+                    [--no-batch-serve]
 
 A step is one pass of the whole hot path over the workload, through the C ABI
-(gc_color_recolor with on-device validation): Random-8 Fit speculative
-coloring to convergence, 10 recoloring iterations in non-increasing class
-size order, and the validation of the result.  Workload: the 27-point stencil
-mesh 128^3 (2,097,152 vertices, 53,645,816 directed CSR entries) with vertex
-ids shuffled by a seed-2 permutation, generated on the GPU.
+(gc_color_recolor with on-device validation), for every leg of the workload.
+The default workload is R-MAT scale 24, edge factor 16, Graph500 parameters
+(0.57, 0.19, 0.19, 0.05), seed 4, deduplicated and symmetrized (16.8 M
+vertices, about 500 M directed CSR entries), generated on the GPU; its two
+legs are First Fit speculative coloring to convergence followed by 20
+recoloring iterations with a seeded random class permutation (RAND), and
+Random-4 Fit followed by the same 20 iterations, each validated on the device.
 
-The metric is GTEPS per color + recolor pass: nnz x (1 + iterations) /
-step time.  `value` has the graph resident in HBM; `e2e` runs the same call
-with host (pinned) buffers, so the graph upload and the color download are
-inside the timed region.  The adjacency (215 MB) is larger than L2 (129 MB),
-so no flush is needed between steps.
+The metric is GTEPS per color + recolor pass: nnz x legs x (1 + iterations)
+/ step time.  `value` has the graph resident in HBM; `e2e` runs the same calls
+with host (pinned) buffers, so the graph uploads and the color downloads are
+inside the timed region.  The adjacency (2 GB) is larger than L2 (129 MB), so
+no flush is needed between steps.  The default line also carries the batched
+engine's record (`batch`: 4,096 graphs in one batch against one call per
+graph) and the serving loop's (`serve`: saturated graphs/s, one call per
+request, and p50/p99 latency under Poisson arrivals), each with its parity
+checks; `--workload batch|serve` prints them as lines of their own.
 
 `--impl reference` times the CPU oracle (the plain single-threaded C
 implementation of the same rules) on a bounded sample of the same workload.
@@ -41,47 +48,60 @@ sys.path.insert(0, ROOT)
 
 import graphgen as gg  # noqa: E402
 
+# A workload is one graph and the legs run on it each step: (strategy, X,
+# seed) colorings, each followed by `iterations` recoloring iterations with
+# permutation `perm` (seed `perm_seed`).  `cpu_graph` is the graph the CPU
+# oracle baseline times the same legs on (a smaller instance of the same
+# generator where the full graph takes the single-threaded oracle minutes);
+# `ref_graph` the one each step of the `--impl reference` arm times.
 WORKLOADS = {
-    "st27-128": dict(graph="st27-128", strategy="RXF", X=8, seed=3, perm="NI", iterations=10,
-                     perm_seed=0,
+    "rmat24": dict(graph="rmat24", legs=[("FF", 1, 7), ("RXF", 4, 7)], perm="RAND", iterations=20,
+                   perm_seed=5, cpu_graph="rmat20", ref_graph="rmat18",
+                   label="R-MAT scale 24 ef 16 (0.57,0.19,0.19,0.05) seed 4, deduplicated and "
+                         "symmetrized; First Fit (seed 7) + 20 RAND recoloring iterations (seed 5), "
+                         "and Random-4 Fit (seed 7) + 20 RAND recoloring iterations (seed 5)"),
+    "st27-128": dict(graph="st27-128", legs=[("RXF", 8, 3)], perm="NI", iterations=10, perm_seed=0,
                      label="27-point stencil 128^3, ids shuffled (seed 2); Random-8 Fit (seed 3) "
                            "+ 10 recoloring iterations NI"),
-    "rmat24": dict(graph="rmat24", strategy="FF", X=1, seed=7, perm="RAND", iterations=20,
-                   perm_seed=5,
-                   label="R-MAT scale 24 ef 16 (0.57,0.19,0.19,0.05) seed 4; First Fit "
-                         "+ 20 recoloring iterations RAND (seed 5)"),
-    "st27-128-quality": dict(graph="st27-128", strategy="RXF", X=5, seed=3, perm="ND", iterations=1,
+    "rmat24-ff": dict(graph="rmat24", legs=[("FF", 1, 7)], perm="RAND", iterations=20, perm_seed=5,
+                      cpu_graph="rmat20", ref_graph="rmat18",
+                      label="R-MAT scale 24 ef 16 (0.57,0.19,0.19,0.05) seed 4; First Fit "
+                            "+ 20 recoloring iterations RAND (seed 5)"),
+    "st27-128-quality": dict(graph="st27-128", legs=[("RXF", 5, 3)], perm="ND", iterations=1,
                              perm_seed=0,
                              label="27-point stencil 128^3, ids shuffled (seed 2); the 'quality' "
                                    "preset: Random-5 Fit (seed 3) + 1 ND iteration"),
-    "rmat24-ndrand": dict(graph="rmat24", strategy="FF", X=1, seed=7, perm="ND-RAND%2^i", iterations=20,
-                          perm_seed=5,
+    "rmat24-ndrand": dict(graph="rmat24", legs=[("FF", 1, 7)], perm="ND-RAND%2^i", iterations=20,
+                          perm_seed=5, cpu_graph="rmat20", ref_graph="rmat18",
                           label="R-MAT scale 24 ef 16 (0.57,0.19,0.19,0.05) seed 4; First Fit + 20 "
                                 "recoloring iterations ND-RAND%2^i (seed 5)"),
-    "rmat-er": dict(graph="rmat-er", strategy="FF", X=1, seed=7, perm="ND", iterations=10, perm_seed=0,
+    "rmat-er": dict(graph="rmat-er", legs=[("FF", 1, 7)], perm="ND", iterations=10, perm_seed=0,
+                    cpu_graph="rmat-er20", ref_graph="rmat-er18",
                     label="RMAT-ER of Table 2: scale 24, edge factor 8, (0.25,0.25,0.25,0.25) seed 4; "
                           "First Fit + 10 ND iterations"),
-    "rmat-good": dict(graph="rmat-good", strategy="FF", X=1, seed=7, perm="ND", iterations=10, perm_seed=0,
+    "rmat-good": dict(graph="rmat-good", legs=[("FF", 1, 7)], perm="ND", iterations=10, perm_seed=0,
+                      cpu_graph="rmat-good20", ref_graph="rmat-good18",
                       label="RMAT-Good of Table 2: scale 24, edge factor 8, (0.45,0.15,0.15,0.25) seed 4; "
                             "First Fit + 10 ND iterations"),
-    "rmat-bad": dict(graph="rmat-bad", strategy="FF", X=1, seed=7, perm="ND", iterations=10, perm_seed=0,
+    "rmat-bad": dict(graph="rmat-bad", legs=[("FF", 1, 7)], perm="ND", iterations=10, perm_seed=0,
+                     cpu_graph="rmat-bad20", ref_graph="rmat-bad18",
                      label="RMAT-Bad of Table 2: scale 24, edge factor 8, (0.55,0.15,0.15,0.15) seed 4; "
                            "First Fit + 10 ND iterations"),
-    "st27-128-lf": dict(graph="st27-128", kind="lf", strategy="RXF", X=8, seed=3, perm="NI", iterations=10,
+    "st27-128-lf": dict(graph="st27-128", kind="lf", legs=[("RXF", 8, 3)], perm="NI", iterations=10,
                         perm_seed=0,
                         label="27-point stencil 128^3, ids shuffled (seed 2); Random-8 Fit with "
                               "Largest-First priorities (seed 3) + 10 NI iterations"),
-    "st27-128-arc": dict(graph="st27-128", kind="arc", strategy="RXF", X=8, seed=3, perm="ND", iterations=10,
+    "st27-128-arc": dict(graph="st27-128", kind="arc", legs=[("RXF", 8, 3)], perm="ND", iterations=10,
                          perm_seed=0,
                          label="27-point stencil 128^3, ids shuffled (seed 2); Random-8 Fit (seed 3) + "
                                "10 asynchronous recoloring (aRC) iterations ND"),
-    "rmat24-arc": dict(graph="rmat24", kind="arc", strategy="FF", X=1, seed=7, perm="ND", iterations=5,
-                       perm_seed=0,
+    "rmat24-arc": dict(graph="rmat24", kind="arc", legs=[("FF", 1, 7)], perm="ND", iterations=5,
+                       perm_seed=0, cpu_graph="rmat20", ref_graph="rmat18",
                        label="R-MAT scale 24 ef 16 (0.57,0.19,0.19,0.05) seed 4; First Fit + 5 "
                              "asynchronous recoloring (aRC) iterations ND"),
     "batch": dict(label="batch"),
     "serve": dict(label="serve"),
-    "er10k": dict(graph="er10k", strategy="FF", X=1, seed=1, perm="RV", iterations=2, perm_seed=0,
+    "er10k": dict(graph="er10k", legs=[("FF", 1, 1)], perm="RV", iterations=2, perm_seed=0,
                   label="Erdos-Renyi n=10,000 mean degree 16 (seed 1); First Fit + 2 iterations RV"),
 }
 METRIC = "GTEPS per color+recolor pass"
@@ -193,41 +213,56 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _oracle_sample(g, wl, passes_recolor):
-    """The CPU oracle on the workload: the speculative coloring pass and
-    `passes_recolor` recoloring iterations.  Returns (seconds, colors, passes)."""
+def _legs(wl):
+    return wl["legs"]
+
+
+def _passes(wl):
+    return len(_legs(wl)) * (1 + wl["iterations"])
+
+
+def _oracle_step(g, wl, passes_recolor=None):
+    """The CPU oracle on graph g: every leg of the workload, its speculative
+    coloring pass and `passes_recolor` (default: the workload's) recoloring
+    iterations.  Returns (seconds, [colors per leg], passes)."""
     import oracle
     off, idx = g.numpy()
-    t0 = time.perf_counter()
-    X = wl["X"] if wl["strategy"] == "RXF" else 1
+    iters = wl["iterations"] if passes_recolor is None else passes_recolor
     kind = wl.get("kind", "rc")
-    if kind == "lf":
-        c, _ = oracle.color_lf(off, idx, X, wl["seed"])
-    else:
-        c, _ = oracle.color(off, idx, X, wl["seed"])
-    if passes_recolor:
-        if kind == "arc":
-            c, _, _ = oracle.recolor_async(off, idx, c, wl["perm"], passes_recolor, wl["perm_seed"])
+    outs = []
+    t0 = time.perf_counter()
+    for strategy, X, seed in _legs(wl):
+        X = X if strategy == "RXF" else 1
+        if kind == "lf":
+            c, _ = oracle.color_lf(off, idx, X, seed)
         else:
-            c, _ = oracle.recolor(off, idx, c, wl["perm"], passes_recolor, wl["perm_seed"])
-    return time.perf_counter() - t0, c, 1 + passes_recolor
+            c, _ = oracle.color(off, idx, X, seed)
+        if iters:
+            if kind == "arc":
+                c, _, _ = oracle.recolor_async(off, idx, c, wl["perm"], iters, wl["perm_seed"])
+            else:
+                c, _ = oracle.recolor(off, idx, c, wl["perm"], iters, wl["perm_seed"])
+        outs.append(c)
+    return time.perf_counter() - t0, outs, len(_legs(wl)) * (1 + iters)
 
 
-def _run_path(gc, off, idx, wl, out):
-    """One pass of the workload's path through the C ABI: the coloring, the
+def _run_leg(gc, off, idx, wl, leg, out):
+    """One leg of the workload's path through the C ABI: the coloring, the
     recoloring iterations and the validation.  Returns (colors, ncolors per
     iteration, stats, validation)."""
+    strategy, X, seed = leg
     kind = wl.get("kind", "rc")
     if kind == "rc":
-        return gc.gc_color_recolor(off, idx, wl["strategy"], wl["X"], wl["seed"], wl["perm"],
-                                   wl["iterations"], wl["perm_seed"], out=out, validate=True)
+        return gc.gc_color_recolor(off, idx, strategy, X, seed, wl["perm"], wl["iterations"],
+                                   wl["perm_seed"], out=out, validate=True)
     if kind == "lf":
-        c, st = gc.gc_color_ordered(off, idx, wl["strategy"], wl["X"], wl["seed"], "LF", out=out)
+        c, st = gc.gc_color_ordered(off, idx, strategy, X, seed, "LF", out=out)
         _, nc, rs = gc.gc_recolor(off, idx, c, wl["perm"], wl["iterations"], wl["perm_seed"], out=out)
     else:
-        c, st = gc.gc_color(off, idx, wl["strategy"], wl["X"], wl["seed"], out=out)
+        c, st = gc.gc_color(off, idx, strategy, X, seed, out=out)
         _, nc, rs = gc.gc_recolor_async(off, idx, c, wl["perm"], wl["iterations"], wl["perm_seed"], out=out)
     st = dict(st)
+    st["edges_examined_recolor"] = rs["edges_examined"]
     st["edges_examined"] += rs["edges_examined"]
     st["iterations"] = wl["iterations"]
     if kind == "arc":
@@ -236,27 +271,56 @@ def _run_path(gc, off, idx, wl, out):
     return out, nc, st, gc.gc_validate(off, idx, out)
 
 
-def run_reference(args, wl, g):
+def _config(wl, n, nnz, ws=1):
+    """The workload description both arms print (identical dicts)."""
+    return {"workload": wl["label"], "n": n, "nnz": nnz, "passes_per_step": _passes(wl),
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+            "legs": [f"{s}{'' if s == 'FF' else '-' + str(x)} seed {sd}" for s, x, sd in _legs(wl)],
+            "recoloring": f"{wl['iterations']} x {wl['perm']} (seed {wl['perm_seed']}) per leg",
+            "validated_each_step": True,
+            "l2": "inputs larger than L2 (adjacency 4*nnz bytes > 129 MB), no flush"
+                  if 4 * nnz > L2_BYTES else "inputs smaller than L2"}
+
+
+def _graph_on(name, prefer_cuda=True):
+    dev = "cuda" if prefer_cuda and torch.cuda.is_available() else "cpu"
+    return gg.workload(name, device=dev).to("cpu")
+
+
+def run_reference(args, wl):
+    """The reference arm: the CPU oracle (single-threaded C, as it stands) on
+    the host cores.  Each step runs every leg of the workload with all its
+    recoloring iterations on `ref_graph`, a smaller instance of the same
+    generator (the full graph's coloring pass alone takes the oracle minutes);
+    the line carries the full workload's config."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    # bounded sample: the coloring pass + one recoloring iteration per step
+    g_full = gg.workload(wl["graph"], device="cuda" if torch.cuda.is_available() else "cpu")
+    n_full, nnz_full = g_full.n, g_full.nnz
+    del g_full
+    torch.cuda.empty_cache() if torch.cuda.is_available() else None
+    ref_name = wl.get("ref_graph", wl["graph"])
+    g = _graph_on(ref_name)
     for _ in range(args.warmup):
-        _oracle_sample(g, wl, 1)
+        _oracle_step(g, wl)
     times = []
     passes = 0
     for _ in range(args.steps):
-        t, _, passes = _oracle_sample(g, wl, 1)
+        t, _, passes = _oracle_step(g, wl)
         times.append(t)
     sec = sum(times) / len(times)
     value = g.nnz * passes / sec / 1e9
-    sample = (f"per step: the {wl['strategy']} coloring pass + 1 {wl['perm']} recoloring iteration "
-              f"of the same graph ({passes} passes of nnz={g.nnz})")
+    where = ("the workload's graph" if ref_name == wl["graph"] else
+             f"{ref_name} (n={g.n}, nnz={g.nnz}; the same generator and parameters at a smaller size)")
+    sample = (f"per step: every leg of the workload ({', '.join(_config(wl, 0, 0)['legs'])}), each "
+              f"coloring pass + {wl['iterations']} {wl['perm']} recoloring iterations, on {where}: "
+              f"{passes} passes per step, single-threaded")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": wl["label"], "n": g.n, "nnz": g.nnz},
+            "config": _config(wl, n_full, nnz_full, ws),
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
@@ -329,7 +393,7 @@ def run_reference_graphs(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def run_batch(args, count=None, nmax=None, steps=None, warmup=None):
     """Batched workload: `batch_count` graphs (half G(n, p) with mean degree
     U[8, 32], half 2D 5-point / 3D 7-point grids, n log-uniform in
     [1e3, batch_nmax], seed 6), each Random-4 Fit + 5 RV recoloring
@@ -341,13 +405,17 @@ def run_batch(args):
     keeps its global index for its seeds, so its colors do not depend on N."""
     import paper_1407_6745_gb300 as gc
     from paper_1407_6745_gb300 import autotune, shard
+    count = args.batch_count if count is None else count
+    nmax = args.batch_nmax if nmax is None else nmax
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     ws, rank, local, dev = _init_ranks()
     gc.load()
     t0 = time.perf_counter()
-    plan = gg.batch_mix_plan(args.batch_count, 6, 1e3, args.batch_nmax)
+    plan = gg.batch_mix_plan(count, 6, 1e3, nmax)
     parts = shard.partition([p[4] for p in plan], ws)
     mine = parts[rank]
-    graphs = gg.batch_mix(args.batch_count, 6, 1e3, args.batch_nmax, device=dev, only=mine)
+    graphs = gg.batch_mix(count, 6, 1e3, nmax, device=dev, only=mine)
     union = gg.batch_union(graphs, device=dev)
     torch.cuda.synchronize(dev)
     torch.cuda.empty_cache()  # generation temporaries back to the device
@@ -358,7 +426,7 @@ def run_batch(args):
     knobs, tuned_ms = autotune.autotune(union.offsets, union.idx, "RXF", 4, 1000, "RV", 5, repeats=1)
     gc.gc_set_tuning(**knobs)
     out = torch.empty(union.n, dtype=torch.int32, device=dev)
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         gc.gc_color_recolor_batch(union.offsets, union.idx, desc, out=out)
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -367,13 +435,13 @@ def run_batch(args):
     torch.cuda.synchronize(dev)
     with Clocks(local) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             _, rounds, maxc, _ = gc.gc_color_recolor_batch(union.offsets, union.idx, desc, out=out)
         e1.record(stream)
         torch.cuda.synchronize(dev)
     _barrier()
     launches = gc.gc_kernel_launches() - launches0
-    batch_ms = shard.max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    batch_ms = shard.max_over_ranks(e0.elapsed_time(e1) / steps)
     # one graph at a time
     outs = [torch.empty(g.n, dtype=torch.int32, device=dev) for g in graphs]
     for g, d, o in zip(graphs, desc, outs):
@@ -408,11 +476,11 @@ def run_batch(args):
     tot_nnz = sum(r["nnz"] for r in rows)
     allmaxc = [m for r in rows for m in r["maxc"]]
     line = {"metric": "batched graphs/s vs one-by-one", "value": total_graphs / (batch_ms * 1e-3),
-            "unit": "graphs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "unit": "graphs/s", "n_gpus": ws, "steps": steps, "warmup": warmup,
             "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": f"batch of {total_graphs} graphs: half G(n,p) mean degree U[8,32], "
-                                   f"half 2D 5-pt / 3D 7-pt grids, n log-uniform [1e3, {args.batch_nmax:g}], "
+                                   f"half 2D 5-pt / 3D 7-pt grids, n log-uniform [1e3, {nmax:g}], "
                                    "Random-4 Fit + 5 RV iterations each", "graphs": total_graphs,
                        "total_n": tot_n, "total_nnz": tot_nnz, "knobs": rows[0]["knobs"],
                        "generation_s": round(max(r["gen_s"] for r in rows), 1),
@@ -427,7 +495,7 @@ def run_batch(args):
             "colors": {"max_after_recoloring_mean": float(np.mean(allmaxc)) if allmaxc else 0.0,
                        "rounds_max": max((m for r in rows for m in r["rounds"]), default=0)},
             "clocks": rows[0]["clocks"], "gpu_launches": sum(r["launches"] for r in rows)}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def serve_pool(count: int, seed: int, device):
@@ -622,7 +690,204 @@ def run_serve(args):
                                                   for r in all_reqs)),
                     "d2h_bytes_per_step": int(4 * n_tot)},
             "clocks": rows[0]["clocks"], "gpu_launches": sum(r["launches"] for r in rows)}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def _log(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
+def _roofline(wl, n, nnz, prof, prof_steps, leg_stats, args):
+    """The dominant kernel's achieved bandwidth on the algorithmic bytes of
+    the hot-path model: a recoloring iteration reads every adjacency id and
+    gathers one neighbor color per entry (8 B per entry) and touches its
+    vertices' offsets, color and class-list entry (24 B per vertex); a
+    speculative pass does the same in both phases of every round for the work
+    set's rows (8 B per examined entry, 24 B per work-set vertex and phase).
+    The DRAM-compulsory part (the ids streamed once, 4 B per entry, plus the
+    16-byte work item per vertex; the gathered colors stay in L2) is reported
+    beside it."""
+    total_ms = sum(v[1] for v in prof.values())
+    top_name, (top_launches, top_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    per_launch_ms = top_ms / top_launches
+    launches_per_step = top_launches / prof_steps
+    kind = wl.get("kind", "rc")
+    iters = wl["iterations"]
+    nlegs = len(_legs(wl))
+    if top_name in ("k_rc_recolor_coop", "k_rc_recolor_step"):
+        per_step = nlegs * iters * (8 * nnz + 24 * n)
+        compulsory = nlegs * iters * (4 * nnz + 16 * n)
+        units = (f"recoloring iterations: 8 B per adjacency entry + 24 B per vertex, "
+                 f"{nlegs} x {iters} x (8*{nnz} + 24*{n}) B per step over {launches_per_step:g} launches")
+    elif top_name in ("spec_rounds_graph", "k_tentative", "k_conflict"):
+        spec_edges, visits = 0, 0
+        for st in leg_stats:
+            spec_edges += st["edges_examined"] - st.get("edges_examined_recolor", iters * nnz if kind != "arc" else 0)
+            colorings = 1 + (iters if kind == "arc" else 0)
+            visits += colorings * n + st["conflicts"] + st.get("conflicts_recolor", 0)
+        # edges_examined counts both phases; 24 B per vertex and phase
+        per_step = 8 * spec_edges + 48 * visits
+        compulsory = 4 * spec_edges + 32 * visits
+        if top_name != "spec_rounds_graph":
+            per_step /= 2
+            compulsory /= 2
+        units = ("speculative rounds: 8 B per examined adjacency entry (both phases) + 24 B per "
+                 f"work-set vertex and phase, {per_step:.4g} B per step over {launches_per_step:g} launches")
+    else:
+        per_step, compulsory = None, None
+        units = "no algorithmic byte count for this kernel"
+    alg_bytes = per_step / launches_per_step if per_step is not None else 0.0
+    comp_bytes = compulsory / launches_per_step if compulsory is not None else 0.0
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = _peak_hbm()
+    return {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": _traffic(top_name, args.workload),
+            "bytes_per_launch": alg_bytes, "units_per_launch": units,
+            "launch_ms": per_launch_ms, "share_of_step": top_ms / total_ms if total_ms else None,
+            "dram_compulsory": {"bytes_per_launch": comp_bytes,
+                                "achieved": comp_bytes / (per_launch_ms * 1e-3) / 1e9,
+                                "frac": comp_bytes / (per_launch_ms * 1e-3) / 1e9 / peak},
+            "kernels": {k: {"launches": v[0] / prof_steps, "ms_per_step": v[1] / prof_steps}
+                        for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+
+
+def run_single(args, wl):
+    """The single-graph workloads (the default: R-MAT scale 24, both legs)."""
+    import paper_1407_6745_gb300 as gc
+    ws, rank, local, dev = _init_ranks()
+    gc.load()
+    t_gen = time.perf_counter()
+    g = gg.workload(wl["graph"], device=dev)
+    torch.cuda.synchronize(dev)
+    _log(f"generated {wl['graph']}: n={g.n} nnz={g.nnz} in {time.perf_counter() - t_gen:.1f} s")
+    off, idx = g.offsets, g.idx
+    n, nnz = g.n, g.nnz
+    legs = _legs(wl)
+    outs = [torch.empty(n, dtype=torch.int32, device=dev) for _ in legs]
+    passes = _passes(wl)
+
+    def step():
+        return [_run_leg(gc, off, idx, wl, leg, o) for leg, o in zip(legs, outs)]
+
+    for _ in range(max(args.warmup, 3)):
+        res = step()
+    for _, _, _, val in res:
+        assert val["n_conflicts"] == 0 and val["n_uncolored"] == 0, val
+    _log("warm-up done")
+
+    # ---- timed region: graph resident in HBM --------------------------------
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = gc.gc_kernel_launches()
+    _barrier()
+    torch.cuda.synchronize(dev)
+    with Clocks(local) as clk:
+        time.sleep(0.5)  # the sampler's first reading lands inside the region
+        e0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    _barrier()
+    launches = gc.gc_kernel_launches() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * nnz * passes / (ms * 1e-3) / 1e9
+    _log(f"timed: {ms:.2f} ms per step, {value:.2f} GTEPS per pass")
+
+    # ---- per-kernel device time (library events on the launching stream) ----
+    gc.gc_profile_enable(True)
+    prof_steps = max(1, min(args.steps, 3))
+    for _ in range(prof_steps):
+        pres = step()
+    prof = gc.gc_profile_read()
+    gc.gc_profile_enable(False)
+    roofline = _roofline(wl, n, nnz, prof, prof_steps, [r[2] for r in pres], args)
+
+    # ---- end to end through the C ABI with host buffers ---------------------
+    e2e = None
+    if not args.no_e2e:
+        off_h = off.cpu().pin_memory()
+        idx_h = idx.cpu().pin_memory()
+        outs_h = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in legs]
+
+        def hstep():
+            return [_run_leg(gc, off_h, idx_h, wl, leg, o) for leg, o in zip(legs, outs_h)]
+        hstep()
+        _barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hstep()
+        torch.cuda.synchronize(dev)
+        e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        if ws > 1:
+            t = torch.tensor([e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_ms = float(t.item())
+        for oh, o in zip(outs_h, outs):
+            assert torch.equal(oh, o.cpu())
+        e2e = {"value": ws * nnz * passes / (e_ms * 1e-3) / 1e9, "unit": "GTEPS",
+               "ms_per_step": e_ms, "h2d_bytes_per_step": len(legs) * (8 * (n + 1) + 4 * nnz),
+               "d2h_bytes_per_step": len(legs) * 4 * n,
+               "how": "one gc_color_recolor call per leg with pinned host buffers: graph upload, "
+                      "coloring, recoloring, validation and color download inside the timed region"}
+        del off_h, idx_h, outs_h
+        _log(f"e2e: {e_ms:.2f} ms per step")
+
+    colors = [{"leg": f"{s}{'' if s == 'FF' else '-' + str(x)}", "after_coloring": r[1][0],
+               "after_recoloring": r[1][-1], "per_iteration": r[1], "rounds": r[2]["rounds"],
+               "edges_examined": r[2]["edges_examined"]}
+              for (s, x, _), r in zip(legs, res)]
+    del g, off, idx
+    torch.cuda.empty_cache()
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1) ------------------------
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1 and rank == 0:
+        cname = wl.get("cpu_graph", wl["graph"])
+        gs = gg.workload(cname, device=dev)
+        gh = gs.to("cpu")
+        sec, ocs, opasses = _oracle_step(gh, wl)
+        same = all(bool(np.array_equal(_run_leg(gc, gs.offsets, gs.idx, wl, leg,
+                                                torch.empty(gs.n, dtype=torch.int32, device=dev))[0]
+                                       .cpu().numpy(), oc))
+                   for leg, oc in zip(legs, ocs))
+        what = ("the same graph" if cname == wl["graph"] else
+                f"{cname} (n={gs.n}, nnz={gs.nnz}), the same generator and parameters at a smaller "
+                f"size: the full graph's coloring pass alone takes the single-threaded oracle minutes")
+        cpu = {"value": gs.nnz * opasses / sec / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"one full step ({opasses} passes: every leg's coloring and recoloring "
+                         f"iterations, no validation pass) on {what}; {sec:.1f} s single-threaded",
+               "parity_bit_exact_on_sample": same}
+        del gs, gh
+        torch.cuda.empty_cache()
+        _log(f"cpu baseline: {sec:.1f} s, parity {same}")
+
+    # ---- many-graph records (batched engine and serving loop) ----------------
+    extra = {}
+    if args.workload == "rmat24" and not args.no_batch_serve:
+        extra["batch"] = run_batch(args, count=args.embed_batch_count, nmax=args.batch_nmax, steps=1,
+                                   warmup=1)
+        _log("batch record done")
+        extra["serve"] = run_serve(args)
+        _log("serve record done")
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": "synthetic",
+                "config": _config(wl, n, nnz, ws),
+                "colors": colors,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk.summary(), "gpu_launches": launches}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
 
 
 def main():
@@ -631,10 +896,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gc", choices=["gc", "reference"])
-    ap.add_argument("--workload", default="st27-128", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch-serve", action="store_true",
+                    help="leave out the batch and serving records of the default line")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--embed-batch-count", type=int, default=4096,
+                    help="graphs of the batch record in the default line")
     ap.add_argument("--batch-nmax", type=float, default=1e6)
     ap.add_argument("--serve-pool", type=int, default=36)
     ap.add_argument("--serve-requests", type=int, default=300)
@@ -651,167 +920,16 @@ def main():
     if args.workload in ("batch", "serve") and args.impl == "reference":
         run_reference_graphs(args)
         return
-    if args.workload in ("batch", "serve"):
-        (run_batch if args.workload == "batch" else run_serve)(args)
-        if torch.distributed.is_available() and torch.distributed.is_initialized():
-            torch.distributed.destroy_process_group()
-        return
-    wl = WORKLOADS[args.workload]
-    ws, rank, local = _dist()
-
     if args.impl == "reference":
-        if rank != 0:
-            return
-        g = gg.workload(wl["graph"], device="cuda" if torch.cuda.is_available() else "cpu").to("cpu")
-        run_reference(args, wl, g)
+        run_reference(args, WORKLOADS[args.workload])
         return
-
-    import paper_1407_6745_gb300 as gc
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    gc.load()
-    g = gg.workload(wl["graph"], device=dev)
-    off, idx = g.offsets, g.idx
-    n, nnz = g.n, g.nnz
-    out = torch.empty(n, dtype=torch.int32, device=dev)
-    passes = 1 + wl["iterations"]
-
-    def step():
-        return _run_path(gc, off, idx, wl, out)
-
-    def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
-
-    for _ in range(max(args.warmup, 3)):
-        _, ncolors, stats, val = step()
-    assert val["n_conflicts"] == 0 and val["n_uncolored"] == 0, val
-
-    # ---- timed region: graph resident in HBM --------------------------------
-    stream = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches0 = gc.gc_kernel_launches()
-    barrier()
-    torch.cuda.synchronize(dev)
-    with Clocks(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            _, ncolors, stats, val = step()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-    barrier()
-    launches = gc.gc_kernel_launches() - launches0
-    ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * nnz * passes / (ms * 1e-3) / 1e9
-
-    # ---- per-kernel device time (library events on the launching stream) ----
-    gc.gc_profile_enable(True)
-    prof_steps = max(1, min(args.steps, 5))
-    for _ in range(prof_steps):
-        _, _, pstats, _ = step()
-    prof = gc.gc_profile_read()
-    gc.gc_profile_enable(False)
-    total_ms = sum(v[1] for v in prof.values())
-    top = max(prof.items(), key=lambda kv: kv[1][1])
-    top_name, (top_launches, top_ms) = top
-    per_launch_ms = top_ms / top_launches
-    # algorithmic bytes per launch of the dominant kernel: its bytes per step
-    # (the units it processes x the bytes per unit) over its launches per step
-    launches_per_step = top_launches / prof_steps
-    kind = wl.get("kind", "rc")
-    if top_name in ("k_rc_recolor_coop", "k_rc_recolor_step"):
-        # per recoloring iteration: every adjacency id once (4 B) and every
-        # vertex's 16-byte work item once
-        per_step = wl["iterations"] * (4 * nnz + 16 * n)
-        units = (f"recoloring iterations: 4 B per adjacency id + 16 B per vertex work item, "
-                 f"{wl['iterations']} x (4*{nnz} + 16*{n}) B per step over "
-                 f"{launches_per_step:g} launches")
-    elif top_name in ("spec_rounds_graph", "k_tentative", "k_conflict"):
-        # speculative rounds: per round and work-set vertex, its row's ids in
-        # both phases (4 B per examined entry) and its 16-byte work item in
-        # both phases; edges_examined and conflicts count exactly those
-        spec_edges = pstats["edges_examined"] - (wl["iterations"] * nnz if kind != "arc" else 0)
-        colorings = 1 + (wl["iterations"] if kind == "arc" else 0)
-        visits = colorings * n + pstats["conflicts"] + pstats.get("conflicts_recolor", 0)
-        per_step = 4 * spec_edges + 32 * visits
-        if top_name != "spec_rounds_graph":
-            per_step /= 2  # one of the two phases
-        units = ("speculative rounds: 4 B per examined adjacency entry + 32 B per work-set visit "
-                 f"(both phases), {per_step:.4g} B per step over {launches_per_step:g} launches")
+    if args.workload in ("batch", "serve"):
+        line = (run_batch if args.workload == "batch" else run_serve)(args)
+        if line is not None:
+            print(json.dumps(line), flush=True)
     else:
-        per_step = None
-        units = "no algorithmic byte count for this kernel"
-    alg_bytes = per_step / launches_per_step if per_step is not None else 0.0
-    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-    peak, peak_kind = _peak_hbm()
-    roofline = {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": _traffic(top_name, args.workload),
-                "bytes_per_launch": alg_bytes, "units_per_launch": units,
-                "launch_ms": per_launch_ms, "share_of_step": top_ms / total_ms if total_ms else None,
-                "kernels": {k: {"launches": v[0] // prof_steps, "ms_per_step": v[1] / prof_steps}
-                            for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
-
-    # ---- end to end through the C ABI with host buffers ---------------------
-    e2e = None
-    if not args.no_e2e:
-        off_h = off.cpu().pin_memory()
-        idx_h = idx.cpu().pin_memory()
-        out_h = torch.empty(n, dtype=torch.int32).pin_memory()
-
-        def hstep():
-            return _run_path(gc, off_h, idx_h, wl, out_h)
-        hstep()
-        barrier()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            hstep()
-        torch.cuda.synchronize(dev)
-        e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-        if ws > 1:
-            t = torch.tensor([e_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_ms = float(t.item())
-        assert torch.equal(out_h, out.cpu())
-        e2e = {"value": ws * nnz * passes / (e_ms * 1e-3) / 1e9, "unit": "GTEPS",
-               "ms_per_step": e_ms, "h2d_bytes_per_step": 8 * (n + 1) + 4 * nnz,
-               "d2h_bytes_per_step": 4 * n}
-
-    # ---- CPU oracle on the host cores (rank 0, N = 1) ------------------------
-    cpu = None
-    if not args.no_cpu_baseline and ws == 1 and rank == 0:
-        gh = g.to("cpu")
-        sec, oc, opasses = _oracle_sample(gh, wl, wl["iterations"])
-        cpu = {"value": nnz * opasses / sec / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-               "sample": f"one full step without the validation pass ({opasses} passes), "
-                         f"{sec:.1f} s single-threaded",
-               "parity_bit_exact": bool(torch.equal(torch.from_numpy(oc), out.cpu()))}
-
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "int32", "data": "synthetic",
-                "config": {"workload": wl["label"], "n": n, "nnz": nnz,
-                           "passes_per_step": passes, "validated_each_step": True,
-                           "l2": "inputs larger than L2 (adjacency 4*nnz bytes > 129 MB)"
-                                 if 4 * nnz > L2_BYTES else "inputs smaller than L2",
-                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-                "colors": {"after_coloring": ncolors[0], "after_recoloring": ncolors[-1],
-                           "per_iteration": ncolors},
-                "rounds": stats["rounds"], "edges_examined_per_step": stats["edges_examined"],
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clk.summary(), "gpu_launches": launches}
-        print(json.dumps(line), flush=True)
-    if ws > 1:
+        run_single(args, WORKLOADS[args.workload])
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
         torch.distributed.destroy_process_group()
 
 
