@@ -60,6 +60,11 @@ WORKLOADS = {
                    label="R-MAT scale 24 ef 16 (0.57,0.19,0.19,0.05) seed 4, deduplicated and "
                          "symmetrized; First Fit (seed 7) + 20 RAND recoloring iterations (seed 5), "
                          "and Random-4 Fit (seed 7) + 20 RAND recoloring iterations (seed 5)"),
+    "rmat22": dict(graph="rmat22", legs=[("FF", 1, 7), ("RXF", 4, 7)], perm="RAND", iterations=20,
+                   perm_seed=5, cpu_graph="rmat18", ref_graph="rmat16",
+                   label="R-MAT scale 22 ef 16 (0.57,0.19,0.19,0.05) seed 4 (the scale-24 workload's "
+                         "legs on a graph a profiler captures whole); First Fit (seed 7) + 20 RAND "
+                         "iterations (seed 5), and Random-4 Fit (seed 7) + 20 RAND iterations (seed 5)"),
     "st27-128": dict(graph="st27-128", legs=[("RXF", 8, 3)], perm="NI", iterations=10, perm_seed=0,
                      label="27-point stencil 128^3, ids shuffled (seed 2); Random-8 Fit (seed 3) "
                            "+ 10 recoloring iterations NI"),
