@@ -913,7 +913,7 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=36)
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-batch", type=int, default=64)
-    ap.add_argument("--serve-workers", type=int, default=2)
+    ap.add_argument("--serve-workers", type=int, default=1)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-check", type=int, default=40)
     ap.add_argument("--tune", default="", help="scheduling knobs, e.g. g2_max_deg=0,recolor_mode=1 "

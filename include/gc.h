@@ -258,16 +258,23 @@ gc_status gc_color_recolor_batch(const gc_graph* g, const gc_batch_graph* graphs
 
 /*
  * Serving: a request loop that colors graphs as they arrive (a library
- * extension, not in the paper).  Submitted requests are queued and admitted
- * first come first served while they fit the device-memory budget and the
- * batch limit; an admitted batch is laid out as one concatenated CSR on the
- * device and colored plus recolored with the batch pipeline, its CSR, colors
- * and work lists resident on the device across all its recoloring
- * iterations.  Several workers (one CUDA stream each) run batches at the same
- * time, so requests that arrive while a batch is on the GPU are admitted into
- * the next one as soon as a worker and memory are free, and the batches
- * overlap on the device.  Every request gets exactly the colors, round count
- * and final max color that gc_color_recolor gives it alone.
+ * extension, not in the paper), with continuous batching.  Submitted
+ * requests are queued and admitted first come first served while they fit
+ * the device-memory budget and the batch limit; the requests admitted
+ * together form a cohort, laid out as one concatenated CSR on the device.
+ * Each worker (one host thread and CUDA stream) keeps up to four cohorts
+ * resident and advances them in turn, one step at a time -- the speculative
+ * coloring of a cohort's graphs, then its recoloring iterations -- with CSR,
+ * colors and work lists resident on the device throughout.  Between steps a
+ * worker admits the requests that arrived meanwhile as a new cohort, as soon
+ * as memory is free, so they do not wait for the graphs already on the GPU;
+ * and a request retires as soon as its own iterations are done: its result
+ * is ready, its latency taken and its scratch share of the budget returned
+ * (its CSR share when its cohort is compacted, once half of the cohort's CSR
+ * belongs to retired requests, or ends).  Workers run their steps on their
+ * own streams, so the work of several cohorts overlaps on the device.  Every
+ * request gets exactly the colors, round count and final max color that
+ * gc_color_recolor gives it alone.
  */
 typedef struct gc_server gc_server;
 
@@ -285,14 +292,15 @@ typedef struct {
     int32_t status;      /* gc_status of the request */
     int32_t rounds;      /* speculative rounds */
     int32_t max_color;   /* after the last recoloring iteration */
-    int32_t batch_size;  /* requests in its batch */
+    int32_t batch_size;  /* requests admitted in its cohort */
     double submit_ms;    /* server clock (ms since gc_server_create) */
-    double start_ms;     /* its batch started */
-    double done_ms;      /* result available */
+    double start_ms;     /* its cohort was admitted */
+    double done_ms;      /* its own iterations done, result available */
 } gc_request_result;
 
 typedef struct {
-    int64_t submitted, completed, rejected, batches;
+    int64_t submitted, completed, rejected;
+    int64_t batches;                 /* cohorts admitted */
     double p50_ms, p99_ms, mean_ms;  /* submit-to-done latency, completed requests */
     double graphs_per_s;             /* completed / (last done - first submit)     */
     int64_t bytes_in_use, bytes_peak;/* admitted device-memory estimate            */
@@ -302,10 +310,11 @@ typedef struct {
  * mem_budget: bytes of device memory the admitted requests may hold at once
  *   (an estimate per request: its CSR and colors plus the larger of the
  *   coloring and the recoloring scratch);
- * max_batch: requests per batch (1..65535); workers: concurrent batches, one
- *   host thread and CUDA stream each (1..64).  With workers > 1 the
- *   recoloring runs stepwise (gc_tuning.recolor_mode = 1), since concurrent
- *   batches share the SMs; otherwise the tuning in force at creation is used.
+ * max_batch: requests per cohort (1..65535); workers: one host thread and
+ *   CUDA stream each (1..64), each with its own cohorts.  The workers use the
+ *   tuning in force at creation.  One worker gives the lowest tail latency
+ *   (its cohorts take turns, the one with the highest response ratio
+ *   first); several overlap their steps on the device.
  * Errors: GC_ERR_INVALID_ARG, GC_ERR_CUDA (no usable device).
  * Every gc_server_* call is thread-safe. */
 gc_status gc_server_create(size_t mem_budget, int32_t max_batch, int32_t workers, gc_server** out);
@@ -313,7 +322,7 @@ gc_status gc_server_create(size_t mem_budget, int32_t max_batch, int32_t workers
  * offsets and ids (host memory -- pinned memory uploads fastest -- or device
  * memory, complete before the call) must stay valid and unchanged until the
  * request's result has been claimed or the server destroyed.  The offsets are
- * checked here, the ids when its batch is staged on the device.  Errors, with
+ * checked here, the ids when its cohort is staged on the device.  Errors, with
  * nothing queued: GC_ERR_INVALID_ARG, GC_ERR_BAD_GRAPH (offsets),
  * GC_ERR_BUDGET (its estimate exceeds mem_budget), GC_ERR_CUDA (reading
  * device offsets).  A request whose ids are malformed finishes with

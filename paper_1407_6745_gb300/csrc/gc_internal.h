@@ -147,6 +147,12 @@ gc_status color_batch_device(const Graph& g, const gc_batch_graph* graphs, int32
 gc_status recolor_batch_device(const Graph& g, const gc_batch_graph* graphs, int32_t ng,
                                const int32_t* colors_in, int32_t* colors_out, int32_t* max_color_out,
                                gc_stats* stats, cudaStream_t s);
+// Recoloring iterations [it_begin, it_end) of a batch in place, on a proper
+// coloring whose per-graph max colors are max_in (trusted: not validated);
+// max_color_out (host, ng entries) receives each graph's max color after.
+gc_status recolor_batch_range(const Graph& g, const gc_batch_graph* graphs, int32_t ng, int32_t* colors,
+                              const int32_t* max_in, int32_t it_begin, int32_t it_end,
+                              int32_t* max_color_out, cudaStream_t s);
 gc_status color_recolor_batch_device(const Graph& g, const gc_batch_graph* graphs, int32_t ng,
                                      int32_t* colors_out, int32_t* rounds_out, int32_t* max_color_out,
                                      gc_stats* stats, cudaStream_t s);

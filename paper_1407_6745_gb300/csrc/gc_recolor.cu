@@ -1114,10 +1114,15 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
 
 // Batch recoloring: every graph recolored with its own permutation, seed and
 // iteration count; a graph past its count keeps its colors.
+// Iterations [it_begin, it_end) of every graph (it_end < 0: to the largest
+// count); a graph whose count is reached keeps its colors.  Running the
+// iterations in several calls gives the same colors as one call: an
+// iteration's class order depends only on the colors it starts from and its
+// own number.
 static gc_status recolor_batch_impl(const Graph& g, const gc_batch_graph* graphs, int32_t ng,
                                     const int32_t* colors_in, bool trusted, const int32_t* max_in,
                                     int32_t* colors_out, int32_t* max_color_out, gc_stats* stats,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, int32_t it_begin = 0, int32_t it_end = -1) {
     int32_t max_x = 1;
     gc_status st = batch_layout(g, graphs, ng, &max_x);
     if (st != GC_OK) return st;
@@ -1125,6 +1130,9 @@ static gc_status recolor_batch_impl(const Graph& g, const gc_batch_graph* graphs
     if (stats) std::memset(stats, 0, sizeof(*stats));
     int32_t iters = 0;
     for (int32_t i = 0; i < ng; ++i) iters = std::max(iters, graphs[i].iterations);
+    if (it_end >= 0) iters = std::min(iters, it_end);
+    it_begin = std::max(it_begin, 0);
+    if (iters < it_begin) iters = it_begin;
     const Tuning tune = recolor_tuning(current_tuning());
     const int grid = persistent_grid(tune);
     const int vgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, grid)));
@@ -1179,7 +1187,7 @@ static gc_status recolor_batch_impl(const Graph& g, const gc_batch_graph* graphs
         cap = std::max(cap, gmax[i]);
     }
     const int64_t T = base[ng];
-    if (iters == 0 || n == 0) {
+    if (iters == it_begin || n == 0) {
         if (colors_out != colors_in && n > 0)
             cudaMemcpyAsync(colors_out, colors_in, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
         if (max_color_out) std::copy(gmax.begin(), gmax.end(), max_color_out);
@@ -1231,8 +1239,8 @@ static gc_status recolor_batch_impl(const Graph& g, const gc_batch_graph* graphs
     int32_t* alt = sc_alt.as<int32_t>();
     const int32_t* cur = colors_in;
     std::vector<int32_t> tp;
-    for (int32_t it = 0; it < iters && st == GC_OK; ++it) {
-        int32_t* dst = (it % 2 == 0) ? alt : colors_out;
+    for (int32_t it = it_begin; it < iters && st == GC_OK; ++it) {
+        int32_t* dst = ((it - it_begin) % 2 == 0) ? alt : colors_out;
         a.iteration = it;
         a.old_c = cur;
         a.new_c = dst;
@@ -1279,7 +1287,7 @@ static gc_status recolor_batch_impl(const Graph& g, const gc_batch_graph* graphs
     if (st == GC_OK && max_color_out)
         st = batch_max_colors(g, a.graph_of, colors_out, nullptr, ng, max_color_out, nullptr, s);
     if (stats) {
-        stats->iterations = iters;
+        stats->iterations = iters - it_begin;
         stats->edges_examined = static_cast<int64_t>(h.edges);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
@@ -1288,6 +1296,13 @@ static gc_status recolor_batch_impl(const Graph& g, const gc_batch_graph* graphs
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
+}
+
+gc_status recolor_batch_range(const Graph& g, const gc_batch_graph* graphs, int32_t ng, int32_t* colors,
+                              const int32_t* max_in, int32_t it_begin, int32_t it_end,
+                              int32_t* max_color_out, cudaStream_t s) {
+    return recolor_batch_impl(g, graphs, ng, colors, true, max_in, colors, max_color_out, nullptr, s,
+                              it_begin, it_end);
 }
 
 gc_status recolor_batch_device(const Graph& g, const gc_batch_graph* graphs, int32_t ng,

@@ -4,22 +4,32 @@
 // A request refers to the caller's CSR (host or device memory, left in place
 // until its result is claimed); submit checks the offsets on the host and
 // queues it.  Workers -- one host thread and one non-blocking CUDA stream
-// each -- take the queue's head requests first come first served while they
-// fit the memory budget and the batch limit, lay them out as one
-// concatenated CSR on the device (one copy per array and request, then a
-// staging kernel that checks every row and shifts each graph's ids and
-// offsets to its place), and run the batch pipeline on it: coloring, then the
-// recoloring iterations with CSR, colors and work lists resident on the
-// device throughout.  The colors come back per request.  While one worker's
-// batch is on the GPU the requests that arrive meanwhile are admitted by the
-// next free worker, so batches overlap on the device and the batch size
-// follows the load.
+// each -- admit the queue's head requests first come first served while they
+// fit the memory budget and the batch limit, as a cohort: one concatenated
+// CSR on the device (one copy per array and request, then a staging kernel
+// that checks every row and shifts each graph's ids and offsets to its
+// place).  A worker keeps several cohorts resident and advances them in
+// turn, one step at a time: the speculative coloring of a cohort's graphs,
+// then recoloring iterations, with CSR, colors and work lists resident on the
+// device throughout.  Between steps it admits the requests that arrived
+// meanwhile as a new cohort (as soon as memory is free), so a request does
+// not wait for the graphs already on the GPU to finish, and a request
+// retires as soon as its own iterations are done: its colors come back, its
+// latency is taken and its scratch share of the budget is returned at once.
+// The CSR of retired requests is returned when its cohort is compacted (once
+// half of its CSR belongs to retired requests) or ends.  A step is the
+// coloring or up to four recoloring iterations, never past the cohort's next
+// retirement, and goes to the worker's cohort with the highest response
+// ratio, (time waited + work left) / work left: a small request admitted
+// behind large ones finishes first, and a large one is not starved.
 //
-// Several batches on the device at once share the SMs, so the workers use the
-// stepwise recoloring form (one launch per class step, no inter-block waits);
-// a single-worker server keeps the tuning it was created with.
+// Workers use the tuning in force at creation.  The dataflow recoloring
+// launch is cooperative: with several workers, one worker's launch waits
+// until every one of its blocks can be resident, so launches of different
+// workers never wait on each other's blocks.
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <condition_variable>
 #include <cstring>
@@ -38,12 +48,13 @@ struct Slot {
     int64_t vbase, ebase, n, nnz;
 };
 
-// Stages a batch: graph y's local offsets (n + 1 of them) sit at
+// Stages a cohort: graph y's local offsets (n + 1 of them) sit at
 // loff[vbase + y ...] and its ids at idx[ebase ...].  One warp per vertex
 // checks the row (the rules of gc_check_graph: offsets from 0 to nnz, never
 // decreasing; ids in [0, n), no self-loop), writes the global offset and
 // shifts the ids by the graph's vertex base.  A graph with a bad row gets
-// bad[y] = 1 (its rows are left unshifted: the batch is run again without it).
+// bad[y] = 1 (its rows are left unshifted: the cohort is staged again
+// without it).
 __global__ void __launch_bounds__(kBlock) k_srv_stage(const int64_t* loff, int64_t* off, int32_t* idx,
                                                       const Slot* slots, int32_t ng, int64_t n_total,
                                                       int64_t nnz_total, int32_t* bad) {
@@ -70,6 +81,38 @@ __global__ void __launch_bounds__(kBlock) k_srv_stage(const int64_t* loff, int64
     if (blockIdx.x == 0 && threadIdx.x == 0) off[n_total] = nnz_total;
 }
 
+// Where a graph kept by a compaction was (o*) and goes (n*).
+struct MoveSlot {
+    int64_t ovbase, oebase, nvbase, nebase, n;
+};
+
+// Compacts a cohort: the graphs kept move to their new vertex and entry
+// bases; one warp per new vertex copies its row with the ids shifted by the
+// change of vertex base, its offset shifted by the change of entry base, and
+// its color.  (The rows were checked when the cohort was staged.)
+__global__ void __launch_bounds__(kBlock) k_srv_compact(const int64_t* off_o, const int32_t* idx_o,
+                                                        const int32_t* col_o, int64_t* off_n, int32_t* idx_n,
+                                                        int32_t* col_n, const MoveSlot* mv, int32_t ng,
+                                                        int64_t n_total, int64_t nnz_total) {
+    const int lane = lane_id();
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * kBlock) >> 5;
+    int32_t y = 0;
+    for (int64_t v = (static_cast<int64_t>(blockIdx.x) * kBlock + threadIdx.x) >> 5; v < n_total; v += nw) {
+        while (y + 1 < ng && mv[y + 1].nvbase <= v) ++y;
+        const MoveSlot m = mv[y];
+        const int64_t ov = m.ovbase + (v - m.nvbase);
+        const int64_t b = off_o[ov], e = off_o[ov + 1];
+        const int64_t nb = b - m.oebase + m.nebase;
+        const int32_t dv = static_cast<int32_t>(m.nvbase - m.ovbase);
+        if (lane == 0) {
+            off_n[v] = nb;
+            col_n[v] = col_o[ov];
+        }
+        for (int64_t k = b + lane; k < e; k += 32) idx_n[nb + (k - b)] = idx_o[k] + dv;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) off_n[n_total] = nnz_total;
+}
+
 using Clock = std::chrono::steady_clock;
 
 struct Request {
@@ -78,14 +121,18 @@ struct Request {
     const int32_t* idx = nullptr;
     int64_t n = 0, nnz = 0;
     int64_t bytes = 0;             // admitted device-memory estimate
+    int64_t resident = 0;          // of which its CSR and colors in its cohort
+    bool solo = false;             // admit alone (a shared cohort ran out of memory)
     gc_batch_graph desc{};
-    // result
+    // result; `status` is read by waiters and written under the server lock
+    // only (finish), from the worker's `outcome`
+    int32_t outcome = GC_OK;
     int32_t status = GC_PENDING;
     std::vector<int32_t> colors;
     gc_request_result res{};
 };
 
-// Device bytes one request holds while its batch runs: its CSR and colors,
+// Device bytes one request holds while its cohort runs: its CSR and colors,
 // the coloring scratch (priority keys, two work lists, buckets, per-vertex
 // graph index and win round) or the recoloring scratch (work list, alternate
 // colors, per-class tables over at most min(n, max degree + X) + 1 classes),
@@ -94,6 +141,57 @@ int64_t request_bytes(int64_t n, int64_t nnz, int64_t max_deg, int32_t X) {
     const int64_t classes = std::min<int64_t>(n, max_deg + X) + 2;
     return 16 * (n + 1) + 4 * nnz + 4 * n + 64 * n + 16 * (nnz / 256 + 1) + 256 * classes + 1024;
 }
+// The part of it that stays with the cohort until compaction: offsets, ids, colors.
+int64_t resident_bytes(int64_t n, int64_t nnz) { return 8 * (n + 1) + 4 * nnz + 4 * n; }
+
+// Requests admitted together, laid out as one concatenated CSR on the device.
+struct Cohort {
+    std::vector<Request*> reqs;
+    std::vector<Slot> slots;
+    std::vector<gc_batch_graph> desc;
+    std::vector<char> live;
+    std::vector<int32_t> rounds, maxc;
+    int32_t iters_done = -1;   // -1: not colored yet; else recoloring iterations done
+    int64_t N = 0, E = 0;
+    Scratch off, idx, col;
+    int64_t resident = 0;          // resident bytes of its requests, live or not
+    int64_t retired_resident = 0;  // of which held for retired requests
+    int32_t admitted = 0;          // requests at admission
+    double start_ms = 0.0;
+    int32_t n_live() const { return static_cast<int32_t>(std::count(live.begin(), live.end(), 1)); }
+    // Work left, in adjacency entries to scan: every live graph's remaining
+    // recoloring iterations, plus its coloring (weighted as a few iterations:
+    // the speculative rounds rescan the rows) if not done yet.
+    double oldest_submit() const {
+        double t = 1e300;
+        for (size_t i = 0; i < reqs.size(); ++i)
+            if (live[i]) t = std::min(t, reqs[i]->res.submit_ms);
+        return t;
+    }
+    double work_left() const {
+        double w = 0.0;
+        for (size_t i = 0; i < reqs.size(); ++i) {
+            if (!live[i]) continue;
+            const double its = desc[i].iterations - std::max(iters_done, 0) + (iters_done < 0 ? 3.0 : 0.0);
+            w += static_cast<double>(slots[i].nnz + slots[i].n) * its;
+        }
+        return w;
+    }
+    Graph graph() const {
+        Graph g{};
+        g.off = off.as<int64_t>();
+        g.idx = idx.as<int32_t>();
+        g.n = static_cast<int32_t>(N);
+        g.nnz = E;
+        g.vec = (reinterpret_cast<uintptr_t>(g.idx) & 15u) == 0;
+        return g;
+    }
+};
+
+constexpr int kCohortsPerWorker = 4;
+// Recoloring iterations in a step at most: a request that arrives meanwhile
+// waits at most that long to be admitted and to take the next step.
+constexpr int32_t kStepIters = 4;
 
 }  // namespace
 }  // namespace gc
@@ -125,171 +223,353 @@ struct gc_server {
         return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
     }
     void worker_main();
-    void run_batch(const std::vector<Request*>& batch, cudaStream_t s, std::vector<gc_status>& each);
+    Cohort* stage(std::vector<Request*> reqs, cudaStream_t s);
+    bool step(Cohort* c, cudaStream_t s);
+    void compact(Cohort* c, cudaStream_t s);
+    // Finishes requests (status, colors already in place) and returns
+    // `release` bytes to the budget.  Takes the lock.
+    void finish(const std::vector<Request*>& done, int64_t release, double start, int32_t size);
+    // Puts requests back at the head of the queue, to be admitted alone.
+    void requeue_solo(const std::vector<Request*>& rs, int64_t release);
 };
 
-// Takes batches off the queue until the server stops and the queue is empty.
+void gc_server::finish(const std::vector<Request*>& done, int64_t release, double start, int32_t size) {
+    const double t = now_ms();
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        in_use -= release;
+        for (Request* r : done) {
+            r->status = r->outcome;
+            r->res.status = r->outcome;
+            r->res.batch_size = size;
+            r->res.start_ms = start;
+            r->res.done_ms = t;
+            if (r->status != GC_OK) r->colors.clear();
+            ++completed;
+            latencies.push_back(t - r->res.submit_ms);
+        }
+        if (!done.empty()) last_done = std::max(last_done, t);
+    }
+    cv_work.notify_all();
+    cv_done.notify_all();
+}
+
+void gc_server::requeue_solo(const std::vector<Request*>& rs, int64_t release) {
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        in_use -= release;
+        for (auto it = rs.rbegin(); it != rs.rend(); ++it) {
+            (*it)->solo = true;
+            queue.push_front(*it);
+        }
+    }
+    cv_work.notify_all();
+}
+
+// Admits batches of the queue as cohorts and advances its cohorts in turn
+// until the server stops and nothing is left.
 void gc_server::worker_main() {
     cudaSetDevice(device);
     set_thread_tuning(&tune);
     cudaStream_t s = nullptr;
     const bool have_stream = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    std::deque<Cohort*> mine;
+    double ms_per_unit = 0.0;  // measured step time per unit of work (Cohort::work_left)
     for (;;) {
         std::vector<Request*> batch;
         int64_t bytes = 0;
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv_work.wait(lk, [&] {
-                return (!queue.empty() && in_use + queue.front()->bytes <= budget) ||
-                       (stopping && queue.empty());
-            });
-            if (queue.empty()) break;  // stopping
-            int64_t n_sum = 0;
-            while (!queue.empty() && static_cast<int32_t>(batch.size()) < max_batch) {
-                Request* r = queue.front();
-                if (in_use + bytes + r->bytes > budget) break;
-                if (n_sum + r->n > INT32_MAX) break;  // the batch CSR numbers vertices in int32
-                queue.pop_front();
-                batch.push_back(r);
-                bytes += r->bytes;
-                n_sum += r->n;
+            auto can_admit = [&] {
+                return !queue.empty() && static_cast<int>(mine.size()) < kCohortsPerWorker &&
+                       in_use + queue.front()->bytes <= budget;
+            };
+            cv_work.wait(lk, [&] { return can_admit() || !mine.empty() || (stopping && queue.empty()); });
+            if (!can_admit() && mine.empty()) break;  // stopping, nothing left
+            if (can_admit()) {
+                int64_t n_sum = 0;
+                while (!queue.empty() && static_cast<int32_t>(batch.size()) < max_batch) {
+                    Request* r = queue.front();
+                    if (in_use + bytes + r->bytes > budget) break;
+                    if (n_sum + r->n > INT32_MAX) break;  // the cohort CSR numbers vertices in int32
+                    if (r->solo && !batch.empty()) break;
+                    queue.pop_front();
+                    batch.push_back(r);
+                    bytes += r->bytes;
+                    n_sum += r->n;
+                    if (r->solo) break;
+                }
+                in_use += bytes;
+                peak = std::max(peak, in_use);
+                ++batches;
             }
-            in_use += bytes;
-            peak = std::max(peak, in_use);
-            ++batches;
         }
-        const double start = now_ms();
-        std::vector<gc_status> each(batch.size(), GC_ERR_CUDA);
-        if (have_stream) run_batch(batch, s, each);
+        if (!batch.empty()) {
+            if (have_stream) {
+                Cohort* c = stage(batch, s);
+                if (c) mine.push_back(c);
+            } else {
+                for (Request* r : batch) r->outcome = GC_ERR_CUDA;
+                finish(batch, bytes, now_ms(), static_cast<int32_t>(batch.size()));
+            }
+        }
+        if (mine.empty()) continue;
+        // highest response ratio next: (time waited + work left) / work left,
+        // the work in ms at the rate this worker has measured.  A small
+        // request admitted behind large ones goes first, and a large one's
+        // ratio grows while it waits, so it is not starved.
+        const double now = now_ms();
+        auto ratio = [&](const Cohort* x) {
+            const double est = std::max(x->work_left() * ms_per_unit, 1e-3);
+            return (now - x->oldest_submit() + est) / est;
+        };
+        auto pick = std::max_element(mine.begin(), mine.end(),
+                                     [&](const Cohort* x, const Cohort* y) { return ratio(x) < ratio(y); });
+        Cohort* c = *pick;
+        mine.erase(pick);
+        const double w0 = c->work_left(), t0 = now_ms();
+        const bool more = step(c, s);
+        const double done_units = w0 - (more ? c->work_left() : 0.0);
+        if (done_units > 0) {  // exponential average of the measured rate
+            const double rate = (now_ms() - t0) / done_units;
+            ms_per_unit = ms_per_unit > 0 ? 0.8 * ms_per_unit + 0.2 * rate : rate;
+        }
+        if (more) mine.push_back(c);
+        else delete c;
         prof_collect();
-        const double done = now_ms();
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            in_use -= bytes;
-            for (size_t i = 0; i < batch.size(); ++i) {
-                Request* r = batch[i];
-                const gc_status st = each[i];
-                r->status = st;
-                r->res.status = st;
-                r->res.batch_size = static_cast<int32_t>(batch.size());
-                r->res.start_ms = start;
-                r->res.done_ms = done;
-                if (st != GC_OK) r->colors.clear();
-                ++completed;
-                latencies.push_back(done - r->res.submit_ms);
-            }
-            last_done = std::max(last_done, done);
-        }
-        cv_work.notify_all();
-        cv_done.notify_all();
     }
     if (have_stream) cudaStreamDestroy(s);
     set_thread_tuning(nullptr);
 }
 
-// Runs one batch; each[i] receives request i's status.  Requests whose CSR
-// fails the staging check get GC_ERR_BAD_GRAPH and the rest run again
-// without them; if the batch does not fit the device's free memory (memory
-// held outside the server), its requests run one at a time.
-void gc_server::run_batch(const std::vector<Request*>& batch, cudaStream_t s,
-                          std::vector<gc_status>& each) {
-    const int32_t ng = static_cast<int32_t>(batch.size());
-    auto fail_all = [&](gc_status st) { std::fill(each.begin(), each.end(), st); };
-    int64_t N = 0, E = 0;
-    std::vector<Slot> slots(ng);
-    std::vector<gc_batch_graph> desc(ng);
-    for (int32_t i = 0; i < ng; ++i) {
-        const Request* r = batch[i];
-        slots[i] = Slot{N, E, r->n, r->nnz};
-        desc[i] = r->desc;
-        desc[i].vertex_base = N;
-        N += r->n;
-        E += r->nnz;
-    }
-    Scratch s_loff, s_off, s_idx, s_col, s_slot, s_bad;
-    auto release = [&] {
-        for (Scratch* x : {&s_loff, &s_off, &s_idx, &s_col, &s_slot, &s_bad}) x->reset();
-    };
-    auto one_at_a_time = [&] {
-        release();
+// Lays requests out as a cohort on the device.  Requests whose CSR fails the
+// staging check finish with GC_ERR_BAD_GRAPH and the rest are staged again
+// without them; if the cohort does not fit the device's free memory (memory
+// held outside the server), its requests go back to the queue to be admitted
+// one at a time.  Returns nullptr when no request is left to run.
+Cohort* gc_server::stage(std::vector<Request*> reqs, cudaStream_t s) {
+    const double start = now_ms();
+    const int32_t admitted = static_cast<int32_t>(reqs.size());
+    for (;;) {
+        const int32_t ng = static_cast<int32_t>(reqs.size());
+        int64_t bytes = 0;
+        for (Request* r : reqs) bytes += r->bytes;
+        auto fail_all = [&](gc_status st) {
+            for (Request* r : reqs) r->outcome = st;
+            finish(reqs, bytes, start, admitted);
+            return nullptr;
+        };
+        Cohort* c = new Cohort();
+        c->reqs = reqs;
+        c->slots.resize(ng);
+        c->desc.resize(ng);
         for (int32_t i = 0; i < ng; ++i) {
-            std::vector<gc_status> one(1);
-            run_batch(std::vector<Request*>{batch[i]}, s, one);
-            each[i] = one[0];
+            const Request* r = reqs[i];
+            c->slots[i] = Slot{c->N, c->E, r->n, r->nnz};
+            c->desc[i] = r->desc;
+            c->desc[i].vertex_base = c->N;
+            c->N += r->n;
+            c->E += r->nnz;
+            c->resident += r->resident;
         }
-    };
-    if (!s_loff.alloc((N + ng) * sizeof(int64_t), s) || !s_off.alloc((N + 1) * sizeof(int64_t), s) ||
-        !s_idx.alloc(E * sizeof(int32_t), s) || !s_col.alloc(N * sizeof(int32_t), s) ||
-        !s_slot.alloc(ng * sizeof(Slot), s) || !s_bad.alloc(ng * sizeof(int32_t), s)) {
-        if (ng == 1) return fail_all(GC_ERR_OOM);
-        return one_at_a_time();
-    }
-    int64_t* loff = s_loff.as<int64_t>();
-    int64_t* off = s_off.as<int64_t>();
-    int32_t* idx = s_idx.as<int32_t>();
-    int32_t* col = s_col.as<int32_t>();
-    int32_t* bad = s_bad.as<int32_t>();
-    cudaError_t e = cudaMemsetAsync(bad, 0, ng * sizeof(int32_t), s);
-    for (int32_t i = 0; i < ng && e == cudaSuccess; ++i) {
-        const Request* r = batch[i];
-        e = cudaMemcpyAsync(loff + slots[i].vbase + i, r->off, (r->n + 1) * sizeof(int64_t),
-                            cudaMemcpyDefault, s);
-        if (e == cudaSuccess && r->nnz > 0)
-            e = cudaMemcpyAsync(idx + slots[i].ebase, r->idx, r->nnz * sizeof(int32_t), cudaMemcpyDefault, s);
-    }
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s_slot.p, slots.data(), ng * sizeof(Slot), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return fail_all(cuda_status(e));
-    const int grid = static_cast<int>(std::max<int64_t>(
-        1, std::min<int64_t>((N * 32 + kBlock - 1) / kBlock, persistent_grid(tune))));
-    GC_LAUNCH(KID_BATCH, s,
-              k_srv_stage<<<grid, kBlock, 0, s>>>(loff, off, idx, s_slot.as<Slot>(), ng, N, E, bad));
-    std::vector<int32_t> hbad(ng, 0);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hbad.data(), bad, ng * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail_all(cuda_status(e));
-    if (std::count(hbad.begin(), hbad.end(), 1) > 0) {
-        std::vector<Request*> good;
-        std::vector<int32_t> where;
+        c->live.assign(ng, 1);
+        c->rounds.assign(ng, 0);
+        c->maxc.assign(ng, 0);
+        c->admitted = admitted;
+        c->start_ms = start;
+        Scratch s_loff, s_slot, s_bad;
+        if (!s_loff.alloc((c->N + ng) * sizeof(int64_t), s) || !c->off.alloc((c->N + 1) * sizeof(int64_t), s) ||
+            !c->idx.alloc(c->E * sizeof(int32_t), s) || !c->col.alloc(c->N * sizeof(int32_t), s) ||
+            !s_slot.alloc(ng * sizeof(Slot), s) || !s_bad.alloc(ng * sizeof(int32_t), s)) {
+            delete c;
+            if (ng == 1) return fail_all(GC_ERR_OOM);
+            requeue_solo(reqs, bytes);
+            return nullptr;
+        }
+        int64_t* loff = s_loff.as<int64_t>();
+        int32_t* bad = s_bad.as<int32_t>();
+        cudaError_t e = cudaMemsetAsync(bad, 0, ng * sizeof(int32_t), s);
+        for (int32_t i = 0; i < ng && e == cudaSuccess; ++i) {
+            const Request* r = reqs[i];
+            e = cudaMemcpyAsync(loff + c->slots[i].vbase + i, r->off, (r->n + 1) * sizeof(int64_t),
+                                cudaMemcpyDefault, s);
+            if (e == cudaSuccess && r->nnz > 0)
+                e = cudaMemcpyAsync(c->idx.as<int32_t>() + c->slots[i].ebase, r->idx, r->nnz * sizeof(int32_t),
+                                    cudaMemcpyDefault, s);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s_slot.p, c->slots.data(), ng * sizeof(Slot), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail_all(cuda_status(e));
+        }
+        const int grid = static_cast<int>(std::max<int64_t>(
+            1, std::min<int64_t>((c->N * 32 + kBlock - 1) / kBlock, persistent_grid(tune))));
+        GC_LAUNCH(KID_BATCH, s,
+                  k_srv_stage<<<grid, kBlock, 0, s>>>(loff, c->off.as<int64_t>(), c->idx.as<int32_t>(),
+                                                       s_slot.as<Slot>(), ng, c->N, c->E, bad));
+        std::vector<int32_t> hbad(ng, 0);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hbad.data(), bad, ng * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail_all(cuda_status(e));
+        }
+        if (std::count(hbad.begin(), hbad.end(), 1) == 0) return c;
+        // bad rows: those requests finish now, the others are staged again
+        delete c;
+        std::vector<Request*> good, badr;
+        int64_t bad_bytes = 0;
         for (int32_t i = 0; i < ng; ++i) {
             if (hbad[i]) {
-                each[i] = GC_ERR_BAD_GRAPH;
+                reqs[i]->outcome = GC_ERR_BAD_GRAPH;
+                badr.push_back(reqs[i]);
+                bad_bytes += reqs[i]->bytes;
             } else {
-                good.push_back(batch[i]);
-                where.push_back(i);
+                good.push_back(reqs[i]);
             }
         }
-        release();
-        if (!good.empty()) {
-            std::vector<gc_status> sub(good.size());
-            run_batch(good, s, sub);
-            for (size_t j = 0; j < good.size(); ++j) each[where[j]] = sub[j];
-        }
-        return;
+        finish(badr, bad_bytes, start, admitted);
+        if (good.empty()) return nullptr;
+        reqs.swap(good);
     }
+}
 
-    Graph g{};
-    g.off = off;
-    g.idx = idx;
-    g.n = static_cast<int32_t>(N);
-    g.nnz = E;
-    g.vec = (reinterpret_cast<uintptr_t>(idx) & 15u) == 0;
-    std::vector<int32_t> rounds(ng, 0), maxc(ng, 0);
-    const gc_status st = color_recolor_batch_device(g, desc.data(), ng, col, rounds.data(), maxc.data(),
-                                                    nullptr, s);
-    if (st == GC_ERR_OOM && ng > 1) return one_at_a_time();
-    if (st != GC_OK) return fail_all(st);
+// One step of a cohort: its coloring, or up to kStepIters recoloring
+// iterations, never past its next retirement; then the requests whose own
+// iterations are done retire.  Returns false once the cohort is over (it is
+// then to be deleted: its memory is returned to the budget here).
+bool gc_server::step(Cohort* c, cudaStream_t s) {
+    const int32_t ng = static_cast<int32_t>(c->reqs.size());
+    const Graph g = c->graph();
+    gc_status st;
+    std::vector<int32_t> maxc_out(ng, 0);
+    if (c->iters_done < 0) {
+        st = color_batch_device(g, c->desc.data(), ng, c->col.as<int32_t>(), c->rounds.data(), maxc_out.data(),
+                                nullptr, s);
+        if (st == GC_OK) c->iters_done = 0;
+    } else {
+        int32_t next = INT32_MAX;
+        for (int32_t i = 0; i < ng; ++i)
+            if (c->live[i]) next = std::min(next, c->desc[i].iterations);
+        const int32_t it1 = std::min(next, c->iters_done + kStepIters);
+        st = recolor_batch_range(g, c->desc.data(), ng, c->col.as<int32_t>(), c->maxc.data(), c->iters_done, it1,
+                                 maxc_out.data(), s);
+        if (st == GC_OK) c->iters_done = it1;
+    }
+    std::vector<Request*> done;
+    int64_t release = 0;
+    if (st != GC_OK) {
+        std::vector<Request*> rest;
+        for (int32_t i = 0; i < ng; ++i)
+            if (c->live[i]) {
+                rest.push_back(c->reqs[i]);
+                release += c->reqs[i]->bytes;
+            }
+        release += c->retired_resident;
+        if (st == GC_ERR_OOM && rest.size() > 1) {
+            requeue_solo(rest, release);  // they start again alone: their results do not depend on it
+        } else {
+            for (Request* r : rest) r->outcome = st;
+            finish(rest, release, c->start_ms, c->admitted);
+        }
+        return false;
+    }
+    c->maxc = maxc_out;
+    cudaError_t e = cudaSuccess;
     for (int32_t i = 0; i < ng && e == cudaSuccess; ++i) {
-        Request* r = batch[i];
+        if (!c->live[i] || c->desc[i].iterations > c->iters_done) continue;
+        Request* r = c->reqs[i];
         r->colors.resize(static_cast<size_t>(r->n));
-        e = cudaMemcpyAsync(r->colors.data(), col + slots[i].vbase, r->n * sizeof(int32_t),
+        e = cudaMemcpyAsync(r->colors.data(), c->col.as<int32_t>() + c->slots[i].vbase, r->n * sizeof(int32_t),
                             cudaMemcpyDeviceToHost, s);
-        r->res.rounds = rounds[i];
-        r->res.max_color = maxc[i];
+        r->res.rounds = c->rounds[i];
+        r->res.max_color = c->maxc[i];
+        r->outcome = GC_OK;
+        c->live[i] = 0;
+        done.push_back(r);
+        release += r->bytes - r->resident;
+        c->retired_resident += r->resident;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    fail_all(cuda_status(e));
+    if (e != cudaSuccess) {
+        for (int32_t i = 0; i < ng; ++i)
+            if (c->live[i]) {
+                done.push_back(c->reqs[i]);
+                release += c->reqs[i]->bytes - c->reqs[i]->resident;
+                c->retired_resident += c->reqs[i]->resident;
+                c->live[i] = 0;
+            }
+        for (Request* r : done) r->outcome = cuda_status(e);
+    }
+    const bool over = c->n_live() == 0;
+    if (over) release += c->retired_resident;
+    finish(done, release, c->start_ms, c->admitted);
+    if (over) return false;
+    if (2 * c->retired_resident >= c->resident) compact(c, s);
+    return true;
+}
+
+// Drops the retired requests from a cohort: the kept graphs move into new,
+// smaller device arrays and the retired ones' CSR returns to the budget.  If
+// the new arrays cannot be had, the cohort stays as it is.
+void gc_server::compact(Cohort* c, cudaStream_t s) {
+    const int32_t ng = static_cast<int32_t>(c->reqs.size());
+    std::vector<MoveSlot> mv;
+    std::vector<int32_t> keep;
+    int64_t N = 0, E = 0;
+    for (int32_t i = 0; i < ng; ++i) {
+        if (!c->live[i]) continue;
+        const Slot& sl = c->slots[i];
+        mv.push_back(MoveSlot{sl.vbase, sl.ebase, N, E, sl.n});
+        keep.push_back(i);
+        N += sl.n;
+        E += sl.nnz;
+    }
+    const int32_t nk = static_cast<int32_t>(keep.size());
+    Scratch off, idx, col, smv;
+    if (!off.alloc((N + 1) * sizeof(int64_t), s) || !idx.alloc(E * sizeof(int32_t), s) ||
+        !col.alloc(N * sizeof(int32_t), s) || !smv.alloc(nk * sizeof(MoveSlot), s))
+        return;
+    if (cudaMemcpyAsync(smv.p, mv.data(), nk * sizeof(MoveSlot), cudaMemcpyHostToDevice, s) != cudaSuccess) return;
+    const int grid = static_cast<int>(
+        std::max<int64_t>(1, std::min<int64_t>((N * 32 + kBlock - 1) / kBlock, persistent_grid(tune))));
+    GC_LAUNCH(KID_BATCH, s,
+              k_srv_compact<<<grid, kBlock, 0, s>>>(c->off.as<int64_t>(), c->idx.as<int32_t>(),
+                                                     c->col.as<int32_t>(), off.as<int64_t>(), idx.as<int32_t>(),
+                                                     col.as<int32_t>(), smv.as<MoveSlot>(), nk, N, E));
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return;
+    std::swap(c->off.p, off.p);
+    std::swap(c->idx.p, idx.p);
+    std::swap(c->col.p, col.p);
+    Cohort k;
+    for (int32_t j = 0; j < nk; ++j) {
+        const int32_t i = keep[j];
+        k.reqs.push_back(c->reqs[i]);
+        k.slots.push_back(Slot{mv[j].nvbase, mv[j].nebase, c->slots[i].n, c->slots[i].nnz});
+        gc_batch_graph d = c->desc[i];
+        d.vertex_base = mv[j].nvbase;
+        k.desc.push_back(d);
+        k.rounds.push_back(c->rounds[i]);
+        k.maxc.push_back(c->maxc[i]);
+    }
+    c->reqs.swap(k.reqs);
+    c->slots.swap(k.slots);
+    c->desc.swap(k.desc);
+    c->rounds.swap(k.rounds);
+    c->maxc.swap(k.maxc);
+    c->live.assign(nk, 1);
+    c->N = N;
+    c->E = E;
+    const int64_t freed = c->retired_resident;
+    c->resident -= freed;
+    c->retired_resident = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        in_use -= freed;
+    }
+    cv_work.notify_all();
 }
 
 namespace {
@@ -336,7 +616,6 @@ gc_status gc_server_create(size_t mem_budget, int32_t max_batch, int32_t workers
     s->budget = static_cast<int64_t>(std::min<size_t>(mem_budget, static_cast<size_t>(INT64_MAX)));
     s->max_batch = max_batch;
     s->tune = current_tuning();
-    if (workers > 1) s->tune.recolor_mode = 1;
     s->t0 = Clock::now();
     for (int32_t i = 0; i < workers; ++i) s->workers.emplace_back([s] { s->worker_main(); });
     *out = s;
@@ -370,6 +649,7 @@ gc_status gc_server_submit(gc_server* s, const gc_request* q, uint64_t* ticket) 
     }
     const int32_t X = q->strategy == GC_FIRST_FIT ? 1 : q->X;
     r->bytes = request_bytes(g.n, g.nnz, max_deg, X);
+    r->resident = resident_bytes(g.n, g.nnz);
     if (st == GC_OK && r->bytes > s->budget) st = GC_ERR_BUDGET;
     if (st != GC_OK) {
         delete r;

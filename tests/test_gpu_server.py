@@ -1,6 +1,7 @@
 """The serving loop (gc_server_*): every request's colors, round count and
 final max color equal what gc_color_recolor gives the same graph alone, for
-requests submitted concurrently and batched however the load falls; budget
+requests submitted concurrently and batched however the load falls; requests
+admitted while others run and retiring with their own iterations; budget
 admission, host-side rejection of bad requests, and the counters."""
 import threading
 
@@ -175,8 +176,8 @@ def test_poll_until_done_and_destroy_with_unclaimed_results():
 
 @pytest.mark.parametrize("device", ["cpu", "cuda"])
 def test_malformed_ids_fail_alone_in_their_batch(device):
-    """Ids are checked when the batch is staged on the device: the request
-    with a bad row finishes with GC_ERR_BAD_GRAPH, the others of its batch
+    """Ids are checked when the cohort is staged on the device: the request
+    with a bad row finishes with GC_ERR_BAD_GRAPH, the others of its cohort
     are colored as if it had not been there."""
     good = [gg.erdos_renyi(4000, 9.0, seed=40 + k) for k in range(5)]
     p = gg.path(6)
@@ -208,3 +209,70 @@ def test_malformed_ids_fail_alone_in_their_batch(device):
                                                   iterations=6, perm_seed=1))
                 assert np.array_equal(col.numpy(), ecol) and res["max_color"] == emax
                 assert res["rounds"] == erounds
+
+
+def _wait_admitted(srv, cohorts, timeout_s=60.0):
+    """Blocks until the server has admitted `cohorts` cohorts."""
+    import time
+    t0 = time.time()
+    while gc.gc_server_stats(srv)["batches"] < cohorts:
+        assert time.time() - t0 < timeout_s, "the server admitted nothing"
+        time.sleep(0.001)
+
+
+def test_request_admitted_while_another_runs():
+    """Continuous batching: a request that arrives while a long one is on the
+    GPU is admitted at the next step boundary (its own cohort, later start),
+    finishes long before the long one, and both get their colors alone."""
+    long_g = gg.rmat(17, 16, 0.57, 0.19, 0.19, seed=11)
+    short_g = gg.erdos_renyi(3000, 10.0, seed=12)
+    long_r = dict(graph=long_g, strategy="FF", X=1, seed=5, perm="RAND", iterations=400, perm_seed=9)
+    short_r = dict(graph=short_g, strategy="RXF", X=3, seed=6, perm="NI", iterations=2, perm_seed=0)
+    with gc.gc_server_create(4 << 30, 8, 1) as srv:
+        tl = _submit(srv, long_r, "cuda")
+        _wait_admitted(srv, 1)
+        ts = _submit(srv, short_r, "cuda")
+        s_col, s_res = gc.gc_server_wait(srv, ts, timeout_ms=120_000)
+        l_col, l_res = gc.gc_server_wait(srv, tl, timeout_ms=300_000)
+        info = gc.gc_server_stats(srv)
+    assert info["batches"] == 2
+    assert s_res["start_ms"] > l_res["start_ms"] and s_res["batch_size"] == 1
+    assert s_res["done_ms"] < l_res["done_ms"], (s_res, l_res)
+    for r, col, res in ((long_r, l_col, l_res), (short_r, s_col, s_res)):
+        ecol, emax, erounds = _alone(r)
+        assert np.array_equal(col.numpy(), ecol) and res["max_color"] == emax and res["rounds"] == erounds
+    # the short request was served by the oracle's rules too
+    off, idx = short_g.numpy()
+    oc, _ = oracle.color(off, idx, 3, 6)
+    orc, _ = oracle.recolor(off, idx, oc, "NI", 2, 0)
+    assert np.array_equal(s_col.numpy(), orc)
+
+
+def test_requests_retire_with_their_own_iterations():
+    """Requests of one cohort retire in the order of their iteration counts,
+    each as soon as its own iterations are done; once most of the cohort has
+    retired it is compacted, and the request still running gets its colors
+    alone all the same (checked against the oracle)."""
+    graphs = [gg.erdos_renyi(40000, 12.0, seed=20 + k) for k in range(4)]
+    iters = [0, 1, 3, 60]
+    reqs = [dict(graph=g, strategy="RXF", X=4, seed=k, perm="RAND", iterations=it, perm_seed=3 + k)
+            for k, (g, it) in enumerate(zip(graphs, iters))]
+    with gc.gc_server_create(4 << 30, 16, 1) as srv:
+        blocker = _submit(srv, dict(graph=graphs[0], strategy="FF", X=1, seed=1, perm="RV", iterations=1,
+                                    perm_seed=0), "cuda")
+        tickets = [_submit(srv, r, "cuda") for r in reqs]  # queued while the blocker runs: one cohort
+        gc.gc_server_wait(srv, blocker, timeout_ms=120_000)
+        out = [gc.gc_server_wait(srv, t, timeout_ms=300_000) for t in tickets]
+        info = gc.gc_server_stats(srv)
+    starts = {res["start_ms"] for _, res in out}
+    done = [res["done_ms"] for _, res in out]
+    for (col, res), r in zip(out, reqs):
+        ecol, emax, erounds = _alone(r)
+        assert np.array_equal(col.numpy(), ecol) and res["max_color"] == emax and res["rounds"] == erounds
+    if len(starts) == 1:  # they formed one cohort (the usual case): retirement order follows iterations
+        assert done == sorted(done) and done[0] < done[-1]
+    off, idx = graphs[3].numpy()
+    oc, _ = oracle.color(off, idx, 4, 3)
+    orc, _ = oracle.recolor(off, idx, oc, "RAND", 60, 6)
+    assert np.array_equal(out[3][0].numpy(), orc)
+    assert info["bytes_in_use"] == 0 and info["completed"] == 5
