@@ -384,7 +384,9 @@ gc_status gc_check_graph(const gc_graph* g, int64_t* first_bad_vertex, void* str
  * setting).  A vertex of degree d with d + X <= 64 is handled by a group of
  * 2 lanes if d <= g2_max_deg, 4 lanes if d <= g4_max_deg, 8 if d <= g8_max_deg, 16 if d <= g16_max_deg,
  * else 32; otherwise by one warp with a shared-memory bitmap if
- * d <= warp_max_deg, else by a whole block (coloring) or split into chunks
+ * d <= warp_max_deg (default 1024; a graph with no row longer than 12288
+ * entries runs the coloring with no limit while warp_max_deg is at its
+ * default), else by a whole block (coloring) or split into chunks
  * of 256 neighbors (recoloring, where rc_warp_max_deg takes the place of
  * warp_max_deg and rc_g2_max_deg, capped at g4_max_deg, that of g2_max_deg).  grid_blocks = 0 sizes every
  * grid to the blocks that fit on the GPU at once.  recolor_mode 0 runs each recoloring iteration as one dataflow

@@ -49,7 +49,7 @@ Tuning default_tuning() {
     t.g4_max_deg = 64;
     t.g8_max_deg = 64;
     t.g16_max_deg = 64;
-    t.warp_max_deg = 1024;
+    t.warp_max_deg = kDefaultWarpMaxDeg;
     t.grid_blocks = 0;
     t.recolor_mode = 0;
     t.spin_limit = 1 << 20;

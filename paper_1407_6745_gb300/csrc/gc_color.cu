@@ -1314,6 +1314,24 @@ static gc_status color_impl(const Graph& g, int32_t X, uint64_t seed, const int3
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) return cuda_status(ce);
         if (h0.err) return status_from_err_bits(h0.err);
+        if (h0.init_cnt[0] > 0 && h0.max_deg <= kPullAllMaxDeg && a.tune.warp_max_deg == kDefaultWarpMaxDeg) {
+            // No row longer than kPullAllMaxDeg: every heavy row is a warp row
+            // that pulls (folds its list of neighbors not yet fixed each
+            // round) instead of being marked.  The marks' extra launch per
+            // round and one pass per fixed vertex cost more than the folds
+            // on such graphs (coloring on GB300: R-MAT 14 2.53 -> 1.93 ms,
+            // R-MAT 16 4.28 -> 3.71 ms, RMAT-Bad 16 1.49 -> 1.36 ms; R-MAT 17,
+            // max degree 15.7 K, 4.97 -> 5.48 ms the other way).  The set-up
+            // runs again with the lifted threshold.
+            a.tune.warp_max_deg = INT32_MAX;
+            cudaMemsetAsync(a.ctrl, 0, sizeof(SpecCtrl), s);
+            GC_LAUNCH(KID_SPEC_SETUP, s, k_spec_setup<<<setup_grid, kBlock, 0, s>>>(a));
+            GC_LAUNCH(KID_SPEC_FILL, s, k_spec_fill<<<setup_grid, kBlock, 0, s>>>(a));
+            ce = cudaMemcpyAsync(&h0, a.ctrl, sizeof(SpecCtrl), cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+            if (ce != cudaSuccess) return cuda_status(ce);
+            if (h0.err) return status_from_err_bits(h0.err);
+        }
         const int32_t nh = h0.init_cnt[0] + h0.init_cnt[1];  // block- and warp-bucket rows
         heavy = nh > 0;
         if (heavy) {

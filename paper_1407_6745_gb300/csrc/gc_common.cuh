@@ -35,6 +35,12 @@ constexpr uint32_t kErrTimeout = 2u;
 constexpr uint32_t kErrImproper = 4u;
 constexpr uint32_t kErrRoundLimit = 8u;
 
+// Default warp threshold of the coloring phase (rows above it take a whole
+// block); on a graph whose largest row has at most kPullAllMaxDeg entries the
+// default is lifted so that every heavy row is a warp row (see color_impl).
+constexpr int32_t kDefaultWarpMaxDeg = 1024;
+constexpr int32_t kPullAllMaxDeg = 12288;
+
 // Scheduling thresholds (runtime; tuned per workload).
 struct Tuning {
     int32_t g4_max_deg;    // deg <= this -> 4 lanes

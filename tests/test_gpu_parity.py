@@ -146,6 +146,17 @@ def test_degree_thresholds(strategy, X):
         _recolor(g, c, perm, 2, 3)
 
 
+def test_pull_form_with_a_marked_block_row():
+    """Warp rows that pull next to one block row (degree 13,000) whose
+    neighbors mark it: the form of a graph with one row above 12,288 entries
+    holding under 1/16 of the entries."""
+    from test_forms import pull_near_graph
+    g = pull_near_graph()
+    for strategy, X in (("FF", 1), ("RXF", 5)):
+        c = _spec(g, strategy, X, 21)
+        _recolor(g, c, "RAND", 2, 4)
+
+
 def test_block_bitmap_window():
     """Random-X draws far past a heavy row's marked bitmap (about degree + 128
     colors): its tentative color comes from the full-row fallback, in 2048-color
