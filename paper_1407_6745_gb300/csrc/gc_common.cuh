@@ -455,8 +455,10 @@ __device__ __forceinline__ int32_t choose_warp(const Graph& g, int64_t beg, int3
 }
 
 // Single ids per lane per batch in the recoloring scans, in units of 4, per
-// group size (32/16/8/4/2 lanes).
-template <int G> struct LanesUnroll { static constexpr int U = (G == 4 || G == 2) ? 2 : 1; };
+// group size (32/16/8/4/2 lanes).  (2 lanes: 4 ids each, rows of at most 16
+// entries; 8 in flight were measured 1-3 % slower on R-MAT, where most of
+// those rows have 1 or 2 entries.)
+template <int G> struct LanesUnroll { static constexpr int U = (G == 4) ? 2 : 1; };
 
 // ---------------------------------------------------------------------------
 // Tiles: a list is cut into segments (one bucket each); segment s holds
