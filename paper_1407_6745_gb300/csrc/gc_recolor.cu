@@ -53,7 +53,7 @@ struct RcCtrl {
     int32_t max_in;       // max input color (validation)
     int32_t n_heavy;      // rows in bucket 0 (split into chunks)
     uint32_t err;
-    int32_t pad;
+    int32_t hot_sg;       // the largest segment of single-entry vertices (scatter)
     unsigned long long edges;
 };
 
@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(kBlock) k_rc_hist(RcArgs a) {
 struct OrderShared {
     int32_t wsum[kOrderThreads / 32];
     int32_t carry;
+    unsigned long long best[kOrderThreads / 32];
     int32_t shuffle[kShuffleSmem];
 };
 
@@ -251,6 +252,7 @@ __device__ __forceinline__ void build_segments(const RcArgs& a, int32_t k, Order
     const int t = threadIdx.x;
     const int32_t nseg = k * kNB;
     int32_t vbase = 0, tbase = 0;
+    unsigned long long best = 0;  // (entries << 32) | segment, over the single-entry buckets
     for (int32_t s0 = 0; s0 < nseg; s0 += kOrderThreads) {
         const int32_t sg = s0 + t;
         int32_t cnt = 0, tiles = 0;
@@ -259,6 +261,10 @@ __device__ __forceinline__ void build_segments(const RcArgs& a, int32_t k, Order
             cnt = units(sg);
             tiles = (cnt + warp_tile(b) - 1) / warp_tile(b);
             a.fill[sg] = 0;
+            if (b != 0) {
+                const unsigned long long key = (static_cast<unsigned long long>(cnt) << 32) | static_cast<uint32_t>(sg);
+                best = key > best ? key : best;
+            }
         }
         int32_t vt, tt;
         const int32_t vp = block_exclusive_scan(cnt, s, vt);
@@ -270,12 +276,21 @@ __device__ __forceinline__ void build_segments(const RcArgs& a, int32_t k, Order
         vbase += vt;
         tbase += tt;
     }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(kFull, best, d);
+        best = o > best ? o : best;
+    }
+    if (lane_id() == 0) s.best[t >> 5] = best;
+    __syncthreads();
     if (t == 0) {
+        for (int w = 0; w < kOrderThreads / 32; ++w) best = s.best[w] > best ? s.best[w] : best;
         a.seg_start[nseg] = vbase;
         a.tile_prefix[nseg] = tbase;
         a.ctrl->k = k;
         a.ctrl->total_tiles = tbase;
         a.ctrl->hub_next = 0;
+        a.ctrl->hot_sg = (best >> 32) ? static_cast<int32_t>(best & 0xffffffffu) : -1;
     }
 }
 
@@ -419,6 +434,21 @@ __device__ __forceinline__ int32_t reserve(int32_t* counter_base, const ScatterI
     return base + __popc(peers & ((1u << lane_id()) - 1u));
 }
 
+// Reserve `units` entries of s_cnt[sg]: the active lanes whose segment is
+// `hot` share one atomic (ballot, not a match), the others take their own.
+__device__ __forceinline__ int32_t hot_or_own(int32_t* s_cnt, int32_t sg, int32_t units, int32_t hot) {
+    const unsigned act = __activemask();
+    const bool is_hot = sg == hot && units == 1;
+    const unsigned hm = __ballot_sync(act, is_hot);
+    if (!is_hot) return atomicAdd(&s_cnt[sg], units);
+    const int l = lane_id();
+    const int leader = __ffs(hm) - 1;
+    int32_t base = 0;
+    if (l == leader) base = atomicAdd(&s_cnt[sg], __popc(hm));
+    base = __shfl_sync(hm, base, leader);
+    return base + __popc(hm & ((1u << l) - 1u));
+}
+
 __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
     __shared__ int32_t s_cnt[kScatterSegs];
     __shared__ int32_t s_base[kScatterSegs];
@@ -442,10 +472,13 @@ __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
         return;
     }
     for (int i = threadIdx.x; i < nseg; i += kBlock) s_cnt[i] = 0;
+    const int32_t hot = a.ctrl->hot_sg;
     __syncthreads();
     // count: the segment and, for a split row, its chunk count (no row read
     // for the others); shared-memory atomics, positions inside a segment are
-    // free (a class is an independent set)
+    // free (a class is an independent set).  The lanes of a warp that fall
+    // into the largest segment (on a skewed graph most vertices do) take
+    // their entries with one atomic.
     for (int64_t i = lo + threadIdx.x; i < hi; i += kBlock) {
         const int32_t v = static_cast<int32_t>(i);
         const int b = a.bucket[v];
@@ -463,7 +496,7 @@ __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
             row_of(a.g, v, beg, deg, &a.ctrl->err);
             units = chunks_of(deg);
         }
-        atomicAdd(&s_cnt[sg], units);
+        hot_or_own(s_cnt, sg, units, hot);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nseg; i += kBlock) {
@@ -479,7 +512,7 @@ __global__ void __launch_bounds__(kBlock) k_rc_scatter(RcArgs a) {
             a.new_c[v] = a.old_c[v];
             continue;
         }
-        const int32_t off = atomicAdd(&s_cnt[si.sg], si.units);
+        const int32_t off = hot_or_own(s_cnt, si.sg, si.units, hot);
         place(a, v, si, s_base[si.sg] + off);
     }
 }
