@@ -26,6 +26,7 @@ def _mixed_batch(count, seed):
     graphs = gg.batch_mix(count, seed, 30, 4000)
     graphs.append(gg.hubs([700, 2500], 3000, seed=seed))   # rows split into chunks when recoloring
     graphs.append(gg.empty(5))
+    graphs.append(gg.workload("rmat12"))  # isolated vertices (722) beside split rows (13)
     rng = np.random.default_rng(seed)
     desc = []
     for i, g in enumerate(graphs):
@@ -66,7 +67,7 @@ def test_batch_equals_alone(knobs):
             ralone, nc, _ = gc.gc_recolor(do, di, alone, d["perm"], d["iterations"], d["perm_seed"])
             assert np.array_equal(rc[lo:hi], ralone.cpu().numpy()), f"graph {i} recoloring"
             assert rmax[i] == nc[-1]
-        if i % 9 == 0 and g.n:  # the oracle on a sample of the graphs
+        if (i % 9 == 0 or i >= len(graphs) - 3) and g.n:  # the oracle on a sample and the special graphs
             off, idx = g.numpy()
             oc, _ = oracle.color(off, idx, d["X"], d["seed"])
             orc, _ = oracle.recolor(off, idx, oc, d["perm"], d["iterations"], d["perm_seed"])
