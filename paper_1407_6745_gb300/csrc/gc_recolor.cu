@@ -120,6 +120,12 @@ __device__ __forceinline__ int32_t ld_relaxed(const int32_t* p) {
 __device__ __forceinline__ void st_relaxed(int32_t* p, int32_t x) {
     asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
 }
+// Adds 1 with acquire-release semantics at GPU scope; returns the old value.
+__device__ __forceinline__ int32_t add_acq_rel(int32_t* p) {
+    int32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+    return old;
+}
 
 __device__ __forceinline__ int32_t chunks_of(int32_t deg) { return (deg + kChunk - 1) / kChunk; }
 
@@ -674,6 +680,14 @@ __device__ __forceinline__ void recolor_group_tile(const RcArgs& a, const Recolo
 
 // One chunk of a split row: the chunk's forbidden colors are OR-ed into the
 // row's bitmap; the warp finishing the last chunk picks the First-Fit color.
+//
+// Ordering: the lanes' OR-s into the row's bitmap precede a warp barrier,
+// and lane 0 then counts the chunk with one acquire-release atomic.  Its
+// release covers the warp's OR-s (the barrier orders them before it); the
+// last chunk's acquire reads the end of the counter's chain of increments,
+// so it sees every chunk's OR-s, and the barrier after it orders the lanes'
+// bitmap reads after it.  (One atomic by one lane instead of a fence by all
+// 32: R-MAT 24 4.86 -> 4.37 ms per iteration, RXF-4 5.17 -> 4.62 ms.)
 template <bool kDataflow>
 __device__ __forceinline__ void recolor_chunk(const RcArgs& a, const RecolorFetch<kDataflow>& f,
                                               const NextHist& nh, const WorkItem& it, uint32_t* bm,
@@ -681,6 +695,9 @@ __device__ __forceinline__ void recolor_chunk(const RcArgs& a, const RecolorFetc
     const int l = lane_id();
     const int32_t slot = -it.v - 1;
     uint32_t* hb = a.hub_bm + static_cast<int64_t>(slot) * a.hub_words;
+    // written by the scatter (an earlier launch): read-only here, loaded early
+    const int32_t nch = l == 0 ? __ldg(a.hub_nch + slot) : 0;
+    const int32_t hv = l == 0 ? __ldg(a.hub_v + slot) : 0;
     static_assert(kWarpBitmapWords == 64, "two bitmap words per lane");
     for (int32_t w0 = 0; w0 < a.hub_words; w0 += kWarpBitmapWords) {
         // The row's bits already merged (read before the scan, in the shadow
@@ -706,12 +723,12 @@ __device__ __forceinline__ void recolor_chunk(const RcArgs& a, const RecolorFetc
         __syncwarp();
     }
     if (l == 0) edges += static_cast<unsigned long long>(it.deg);
-    __threadfence();
+    __syncwarp();
     int last = 0;
-    if (l == 0) last = atomicAdd(&a.hub_done[slot], 1) == a.hub_nch[slot] - 1;
+    if (l == 0) last = add_acq_rel(a.hub_done + slot) == nch - 1;
     last = __shfl_sync(kFull, last, 0);
+    __syncwarp();
     if (!last) return;
-    __threadfence();
     // First Fit over the merged bitmap: the first clear bit
     for (int32_t w0 = 0; w0 < a.hub_words; w0 += 32) {
         const int32_t i = w0 + l;
@@ -722,9 +739,9 @@ __device__ __forceinline__ void recolor_chunk(const RcArgs& a, const RecolorFetc
             const uint32_t fw = __shfl_sync(kFull, free_bits, src);
             const int32_t c = (w0 + src) * 32 + __ffs(fw);
             if (l == 0) {
-                st_relaxed(a.new_c + a.hub_v[slot], c);
+                st_relaxed(a.new_c + hv, c);
                 my_max = max(my_max, c);
-                nh.add(c, 0, a.hub_nch[slot]);
+                nh.add(c, 0, nch);
             }
             return;
         }
