@@ -34,6 +34,9 @@ def _mixed_batch(count, seed):
                          perm=["RV", "NI", "ND", "RAND", "ND-RAND%2", "ND-RAND%2^i"][i % 6],
                          iterations=int(rng.integers(0, 6)),
                          perm_seed=int(rng.integers(1 << 40))))
+    # the isolated vertices of a graph with no recoloring iteration keep their
+    # Random-8 Fit colors (a finished graph, not color 1)
+    desc[-2].update(X=8, iterations=0)
     return graphs, desc
 
 
