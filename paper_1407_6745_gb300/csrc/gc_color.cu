@@ -609,13 +609,20 @@ __global__ void __launch_bounds__(kBlock, 5) k_tentative(SpecArgs a) {
             if (k < rt.cnt[b]) {
                 const WorkItem it = load_item(list + rt.start[b] + k);
                 const uint32_t j = kRXF ? draw_index(a, it.v, round) : 0u;
-                int32_t c = b == 0 || !a.heavy->pull_warp ? choose_bitmap_warp(*a.heavy, it.v, j)
-                                                          : choose_warp_pending(a, it, j, s_bm[w]);
+                // a marking row's item holds its list (ListItem), and the
+                // conflict launch counts this visit's entries with its own
+                const bool marked = b == 0 || !a.heavy->pull_warp;
+                int32_t c = marked ? choose_bitmap_warp(*a.heavy, it.v, j) : choose_warp_pending(a, it, j, s_bm[w]);
                 // past the bitmap's free colors (Random-X with a large X): the row in full
-                if (c < 0) c = choose_warp<4>(a.g, it.beg, it.deg, j, fetch, s_bm[w], &a.ctrl->err);
+                if (c < 0) {
+                    int64_t rbeg = it.beg;
+                    int32_t rdeg = it.deg;
+                    if (marked) row_of(a.g, it.v, rbeg, rdeg, &a.ctrl->err);
+                    c = choose_warp<4>(a.g, rbeg, rdeg, j, fetch, s_bm[w], &a.ctrl->err);
+                }
                 if (lane_id() == 0) {
                     set_tent(a, it.v, c);
-                    edges += static_cast<unsigned long long>(it.deg);
+                    if (!marked) edges += static_cast<unsigned long long>(it.deg);
                 }
             }
             break;
@@ -658,14 +665,27 @@ __device__ __forceinline__ bool loses(const SpecArgs& a, const WorkItem& it, int
     return lose;
 }
 
+// ListItem: from round 1 on, the work item of a marking heavy row (a
+// block-bucket row, or a warp-bucket row where the warp rows do not pull)
+// holds its list instead of its row: beg = the list's start in pend, deg =
+// its length.  A visit then reads the item, the list and the listed keys
+// with no index lookups in between (before: item, heavy index, list start
+// and length, list, keys); the row's bounds, needed only for the edge count
+// and a winner's marks, are loaded beside the list (the conflict launch
+// counts both launches' entries of such a row: every row of a round's work
+// set is visited by both).  Round 0 reads rows from items of the usual form,
+// and its losers write the new one.
+
 // Round 0, a block-bucket row (the whole block): the conflict test over the
 // full row, which also writes the row's list: its neighbors above it in the
 // total order that are not fixed.  Only these can beat it in a later round.
+// lbeg, lcnt: the list's start in pend and its length (block-uniform).
 __device__ bool above_build_block(const SpecArgs& a, const HeavyRows& hr, const WorkItem& it,
-                                  uint32_t* wsum) {
+                                  uint32_t* wsum, int64_t& lbeg, int32_t& lcnt) {
     const int t = threadIdx.x, l = lane_id(), w = t >> 5;
     const int32_t h = hr.hid[it.v];
-    int32_t* dst = hr.pend + hr.h_pbeg[h];
+    lbeg = hr.h_pbeg[h];
+    int32_t* dst = hr.pend + lbeg;
     const unsigned long long* key = reinterpret_cast<const unsigned long long*>(a.key);
     const uint64_t kv = __ldg(key + it.v);
     const uint32_t tv = key_tent(kv);
@@ -713,7 +733,7 @@ __device__ bool above_build_block(const SpecArgs& a, const HeavyRows& hr, const 
         kept += total;
         __syncthreads();
     }
-    if (t == 0) hr.h_pcnt[h] = kept;
+    lcnt = kept;
     if (loop) atomicOr(&a.ctrl->err, kErrBadGraph);
     return lose;
 }
@@ -728,15 +748,16 @@ __device__ bool above_build_block(const SpecArgs& a, const HeavyRows& hr, const 
 // usually to one of the first entries, and a loss found there leaves the
 // list as it is (still a superset of the neighbors above v not fixed).
 // Every kCompactEvery-th round skips the probe, so that no list goes long
-// uncompacted.
-__device__ bool above_scan_block(const SpecArgs& a, const HeavyRows& hr, const WorkItem& it,
-                                 int32_t (*stage)[kHeavyStep], uint32_t* wsum) {
+// uncompacted.  The item holds the list (see ListItem); lcnt: its length
+// after the scan (block-uniform).
+__device__ bool above_scan_block(const SpecArgs& a, const WorkItem& it, int32_t (*stage)[kHeavyStep],
+                                 uint32_t* wsum, int32_t& lcnt) {
     const int t = threadIdx.x, l = lane_id(), w = t >> 5;
-    const int32_t h = hr.hid[it.v];
-    const int64_t pc = hr.h_pcnt[h];
-    int32_t* lst = hr.pend + hr.h_pbeg[h];
+    const int64_t pc = it.deg;
+    int32_t* lst = a.heavy->pend + it.beg;
     const unsigned long long* key = reinterpret_cast<const unsigned long long*>(a.key);
     const uint32_t tv = key_tent(__ldg(key + it.v));
+    lcnt = static_cast<int32_t>(pc);
     if (pc > kProbeMin * kBlock && (a.ctrl->round & (kCompactEvery - 1)) != 0) {  // the probe
         bool hit = false;
         const int32_t u = lst[t];
@@ -792,7 +813,7 @@ __device__ bool above_scan_block(const SpecArgs& a, const HeavyRows& hr, const W
         kept += total;
         __syncthreads();  // frees stage[parity] for the step after next
     }
-    if (t == 0) hr.h_pcnt[h] = kept;
+    lcnt = kept;
     return lose;
 }
 
@@ -801,10 +822,12 @@ __device__ bool above_scan_block(const SpecArgs& a, const HeavyRows& hr, const W
 // batch's reads precede its writes, which land at or below every position
 // the batch read), after a probe of the first 32 entries as in
 // above_scan_block.
-__device__ bool above_build_warp(const SpecArgs& a, const HeavyRows& hr, const WorkItem& it) {
+__device__ bool above_build_warp(const SpecArgs& a, const HeavyRows& hr, const WorkItem& it, int64_t& lbeg,
+                                 int32_t& lcnt) {
     const int l = lane_id();
     const int32_t h = hr.hid[it.v];
-    int32_t* dst = hr.pend + hr.h_pbeg[h];
+    lbeg = hr.h_pbeg[h];
+    int32_t* dst = hr.pend + lbeg;
     const unsigned long long* key = reinterpret_cast<const unsigned long long*>(a.key);
     const uint64_t kv = __ldg(key + it.v);
     const uint32_t tv = key_tent(kv);
@@ -835,18 +858,18 @@ __device__ bool above_build_warp(const SpecArgs& a, const HeavyRows& hr, const W
             kept += __popc(bal);
         }
     }
-    if (l == 0) hr.h_pcnt[h] = kept;
+    lcnt = kept;
     if (loop) atomicOr(&a.ctrl->err, kErrBadGraph);
     return __any_sync(kFull, lose);
 }
 
-__device__ bool above_scan_warp(const SpecArgs& a, const HeavyRows& hr, const WorkItem& it) {
+__device__ bool above_scan_warp(const SpecArgs& a, const WorkItem& it, int32_t& lcnt) {
     const int l = lane_id();
-    const int32_t h = hr.hid[it.v];
-    const int32_t pc = hr.h_pcnt[h];
-    int32_t* lst = hr.pend + hr.h_pbeg[h];
+    const int32_t pc = it.deg;
+    int32_t* lst = a.heavy->pend + it.beg;
     const unsigned long long* key = reinterpret_cast<const unsigned long long*>(a.key);
     const uint32_t tv = key_tent(__ldg(key + it.v));
+    lcnt = pc;
     if (pc > kProbeMin * 32 && (a.ctrl->round & (kCompactEvery - 1)) != 0) {  // the probe
         const int32_t u = lst[l];
         const bool hit = static_cast<uint32_t>(u) < static_cast<uint32_t>(a.g.n) &&
@@ -883,7 +906,7 @@ __device__ bool above_scan_warp(const SpecArgs& a, const HeavyRows& hr, const Wo
             kept += __popc(bal);
         }
     }
-    if (l == 0) hr.h_pcnt[h] = kept;
+    lcnt = kept;
     return __any_sync(kFull, lose);
 }
 
@@ -987,24 +1010,35 @@ __device__ __forceinline__ void conflict_warp_tile(const SpecArgs& a, const Heav
     const bool valid = k < rt.cnt[1];  // the same for the whole warp
     WorkItem it{0, 0, 0};
     bool lose = false;
+    int64_t rbeg = 0, lbeg = 0;  // the row (edge count, marks) and the list (next round's item)
+    int32_t rdeg = 0, lcnt = 0;
     if (valid) {
         it = load_item(list + rt.start[1] + k);
-        lose = round == 0 ? above_build_warp(a, hr, it) : above_scan_warp(a, hr, it);
+        if (round == 0) {
+            rbeg = it.beg;
+            rdeg = it.deg;
+            lose = above_build_warp(a, hr, it, lbeg, lcnt);
+        } else {
+            row_of(a.g, it.v, rbeg, rdeg, &a.ctrl->err);  // loaded beside the list
+            lbeg = it.beg;
+            lose = above_scan_warp(a, it, lcnt);
+        }
     }
     const bool leader = valid && lane_id() == 0;
     const bool win = valid && !lose;
     int32_t c = 0;
     if (leader) {
-        edges += static_cast<unsigned long long>(it.deg);
+        // from round 1 on also the round's tentative visit (ListItem)
+        edges += static_cast<unsigned long long>(rdeg) * (round == 0 ? 1u : 2u);
         if (win) c = static_cast<int32_t>(key_tent(a.key[it.v]));
     }
     fix_color<true>(a, it.v, c, leader && win, my_max, round);
     if (leader && win) a.bucket[it.v] = kBucketFixed;
     if (hr.bref) {  // a warp-bucket row's graph has heavy rows: it marks
         c = __shfl_sync(kFull, c, 0);
-        if (win) mark_color(a, hr, it.beg, it.deg, c, lane_id(), 32);
+        if (win) mark_color(a, hr, rbeg, rdeg, c, lane_id(), 32);
     }
-    warp_append(leader && lose, it.beg, it.v, it.deg, &a.ctrl->cnt[par ^ 1][1], next, rt.start[1]);
+    warp_append(leader && lose, lbeg, it.v, lcnt, &a.ctrl->cnt[par ^ 1][1], next, rt.start[1]);
 }
 
 // kHeavy = false: the form for graphs without heavy rows (buckets 0 and 1
@@ -1017,7 +1051,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_conflict(SpecArgs a) {
     __shared__ RoundTiles rt;
     __shared__ bool s_last;
     __shared__ uint32_t s_wsum[kWarps];
-    __shared__ int32_t s_c, s_pos;
+    __shared__ int32_t s_c, s_pos, s_rdeg;
+    __shared__ int64_t s_rbeg;
     __shared__ __align__(16) int32_t stage[2][kHeavyStep];  // block-bucket rows' next list step
     const int32_t round = a.ctrl->round;
     const int par = round & 1;
@@ -1037,29 +1072,35 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_conflict(SpecArgs a) {
         if constexpr (kHeavy) {
             if (b == 0) {
             const WorkItem it = load_item(list + rt.start[0] + first);
-            const bool mine = round == 0 ? above_build_block(a, hr, it, s_wsum)
-                                         : above_scan_block(a, hr, it, stage, s_wsum);
+            int64_t rbeg = it.beg, lbeg = it.beg;  // the row and the list (see ListItem)
+            int32_t rdeg = it.deg, lcnt = 0;
+            if (round != 0 && threadIdx.x == 0) row_of(a.g, it.v, rbeg, rdeg, &a.ctrl->err);
+            const bool mine = round == 0 ? above_build_block(a, hr, it, s_wsum, lbeg, lcnt)
+                                         : above_scan_block(a, it, stage, s_wsum, lcnt);
             const bool lose = __syncthreads_or(mine);
             if (threadIdx.x == 0) {
-                edges += static_cast<unsigned long long>(it.deg);
+                // from round 1 on also the round's tentative visit (ListItem)
+                edges += static_cast<unsigned long long>(rdeg) * (round == 0 ? 1u : 2u);
+                s_rdeg = rdeg;
+                s_rbeg = rbeg;
                 if (lose) {
                     const int32_t pos = atomicAdd(&a.ctrl->cnt[par ^ 1][0], 1);
-                    store_item(next + rt.start[0] + pos, it.beg, it.v, it.deg);
+                    store_item(next + rt.start[0] + pos, lbeg, it.v, lcnt);
                 } else {
                     s_c = static_cast<int32_t>(key_tent(a.key[it.v]));
                     fix_color<true>(a, it.v, s_c, true, my_max, round);
                     a.bucket[it.v] = kBucketFixed;
                     // the row's marks go to the grid-wide marking launch
-                    const int32_t pieces = (it.deg + kMarkChunk - 1) / kMarkChunk;
+                    const int32_t pieces = (rdeg + kMarkChunk - 1) / kMarkChunk;
                     s_pos = pieces ? atomicAdd(&a.ctrl->mark_cnt, pieces) : 0;
                 }
             }
             __syncthreads();
             if (!lose) {
-                const int32_t pieces = (it.deg + kMarkChunk - 1) / kMarkChunk;
+                const int32_t pieces = (s_rdeg + kMarkChunk - 1) / kMarkChunk;
                 for (int32_t q = threadIdx.x; q < pieces && s_pos + q < hr.mark_cap; q += kBlock) {
-                    const int32_t len = min(kMarkChunk, it.deg - q * kMarkChunk);
-                    store_item(hr.mark + s_pos + q, it.beg + static_cast<int64_t>(q) * kMarkChunk, s_c, len);
+                    const int32_t len = min(kMarkChunk, s_rdeg - q * kMarkChunk);
+                    store_item(hr.mark + s_pos + q, s_rbeg + static_cast<int64_t>(q) * kMarkChunk, s_c, len);
                 }
             }
             __syncthreads();  // s_c, s_pos and the stage buffers are reused by the next tile
