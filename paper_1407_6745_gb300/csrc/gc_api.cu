@@ -58,7 +58,7 @@ Tuning default_tuning() {
     // 2 lanes up to degree 32 when coloring, 16 when recoloring (measured:
     // stencil coloring 1.32 -> 1.15 ms at 32, its recoloring 3.24 -> 4.61 ms)
     t.g2_max_deg = 32;
-    t.rc_g2_max_deg = 16;
+    t.rc_g2_max_deg = kDefaultRcG2MaxDeg;
     return t;
 }
 Tuning g_tune = default_tuning();

@@ -40,6 +40,10 @@ constexpr uint32_t kErrRoundLimit = 8u;
 // default is lifted so that every heavy row is a warp row (see color_impl).
 constexpr int32_t kDefaultWarpMaxDeg = 1024;
 constexpr int32_t kPullAllMaxDeg = 12288;
+// Default 2-lane threshold of the recoloring phase, and the one a recoloring
+// launch bound by its class chain takes instead (see recolor_device).
+constexpr int32_t kDefaultRcG2MaxDeg = 16;
+constexpr int32_t kChainRcG2MaxDeg = 8;
 
 // Scheduling thresholds (runtime; tuned per workload).
 struct Tuning {

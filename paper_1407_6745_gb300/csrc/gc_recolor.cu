@@ -1086,6 +1086,18 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
     a.bucket = sc_bucket.as<uint8_t>();
     a.ctrl = sc_ctrl.as<RcCtrl>();
     cudaMemsetAsync(a.ctrl, 0, sizeof(RcCtrl), s);
+    // A launch that gets fewer blocks than fit is bound by its class chain
+    // (coop_grid); there a row of 9 to 16 entries takes 4 lanes (one batch of
+    // loads) instead of 2 (two batches), unless the caller set the 2-lane
+    // threshold.  Per iteration, G(10^4, 16): 86 -> 51 us; a large graph is
+    // bound by tile throughput and keeps 2 lanes (RMAT-ER at scale 24 went
+    // 2.08 -> 3.09 ms with 4).
+    const bool g2_default = current_tuning().rc_g2_max_deg == kDefaultRcG2MaxDeg;
+    const int coop_fit = sm_count() * occupancy_of(reinterpret_cast<const void*>(k_rc_recolor_coop), kBlock);
+    auto chain_bound = [&](int32_t maxc) {
+        return g2_default && coop_grid(g.nnz, std::max(maxc, 1), coop_fit) < coop_fit;
+    };
+    if (trusted && chain_bound(maxc_in)) a.tune.g2_max_deg = std::min(kChainRcG2MaxDeg, a.tune.g4_max_deg);
     RcCtrl h;
     std::memset(&h, 0, sizeof(h));
     if (n > 0) {
@@ -1106,7 +1118,14 @@ gc_status recolor_device(const Graph& g, const int32_t* colors_in, int32_t maxc_
         if (ce != cudaSuccess) return cuda_status(ce);
         if (h.err & kErrBadGraph) return GC_ERR_BAD_GRAPH;
         if (h.err & kErrImproper) return GC_ERR_IMPROPER_INPUT;
-        if (!trusted) maxc_in = h.max_in;
+        if (!trusted) {
+            maxc_in = h.max_in;
+            if (n > 0 && chain_bound(maxc_in)) {  // the buckets again, with the chain-bound threshold
+                a.tune.g2_max_deg = std::min(kChainRcG2MaxDeg, a.tune.g4_max_deg);
+                cudaMemsetAsync(&a.ctrl->n_heavy, 0, sizeof(int32_t), s);
+                GC_LAUNCH(KID_RC_BUCKET, s, k_rc_bucket<<<vgrid, kBlock, 0, s>>>(a));
+            }
+        }
     } else {
         h.n_heavy = static_cast<int32_t>(heavy_bound);
     }
