@@ -388,7 +388,9 @@ gc_status gc_check_graph(const gc_graph* g, int64_t* first_bad_vertex, void* str
  * entries runs the coloring with no limit while warp_max_deg is at its
  * default), else by a whole block (coloring) or split into chunks
  * of 256 neighbors (recoloring, where rc_warp_max_deg takes the place of
- * warp_max_deg and rc_g2_max_deg, capped at g4_max_deg, that of g2_max_deg).  grid_blocks = 0 sizes every
+ * warp_max_deg and rc_g2_max_deg, capped at g4_max_deg, that of g2_max_deg;
+ * while rc_g2_max_deg holds its default of 16, a recoloring launch bound by
+ * its class chain, one given fewer blocks than fit, takes 8).  grid_blocks = 0 sizes every
  * grid to the blocks that fit on the GPU at once.  recolor_mode 0 runs each recoloring iteration as one dataflow
  * launch (vertices wait, with a bounded spin of spin_limit polls, for their
  * earlier-class neighbors); 1 launches one grid per color class.

@@ -193,6 +193,8 @@ def test_complete_graph_crosses_register_window():
     dict(rc_warp_max_deg=0),
     dict(rc_warp_max_deg=1 << 30),
     dict(rc_g2_max_deg=0),
+    dict(rc_g2_max_deg=8),    # the value a chain-bound launch takes by default
+    dict(rc_g2_max_deg=15),   # about the default of a launch not bound by its chain
     dict(rc_g2_max_deg=64, g2_max_deg=0),
     dict(g2_max_deg=16, rc_g2_max_deg=32),
 ])
