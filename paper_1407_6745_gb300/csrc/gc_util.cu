@@ -17,12 +17,22 @@ struct ValCtrl {
     int32_t max_color;
     uint32_t err;
     unsigned long long distinct;
-    int32_t heavy;          // rows deferred to the block-per-row pass
+    int32_t heavy;          // rows deferred to the block-per-row pass (gc_validate: to the warp-per-row one)
     int32_t big_colors;     // vertices with a color >= kPresColors
+    int32_t big;            // gc_validate: pieces of the rows beyond kValWarpDeg
 };
 
 constexpr int kValG = 4;                 // lanes per light row (measured: 8 -> 4 saves 30 us on the stencil)
-constexpr int32_t kHeavyDeg = 256;       // heavier rows: one block each
+constexpr int32_t kHeavyDeg = 256;       // heavier rows: one block each (gc_validate_noalloc)
+// gc_validate: rows of up to kValLightDeg entries take kValG lanes (one
+// pass of loads), up to kValWarpDeg a warp, longer ones a block.  (R-MAT
+// scale 24: 2.77 + 1.60 ms with the noalloc form's split at 256 entries.)
+constexpr int32_t kValLightDeg = 64;
+constexpr int32_t kValWarpDeg = 4096;
+// Rows beyond kValWarpDeg are cut into pieces of kValPiece entries, a block
+// each (the largest R-MAT rows hold hundreds of thousands of entries; one
+// block per row left a single block walking the largest).
+constexpr int32_t kValPiece = 4096;
 constexpr int kPresWords = 2048;         // presence bitmap of colors < 65536
 constexpr int32_t kPresColors = kPresWords * 32;
 
@@ -32,6 +42,8 @@ struct ValArgs {
     ValCtrl* c;
     uint32_t* pres;    // kPresWords
     int32_t* heavy;    // n
+    int2* pieces;      // gc_validate: (row, piece index) of the rows beyond kValWarpDeg
+    int64_t piece_cap;
 };
 
 // Count of neighbors with v's color in this lane's stripe.
@@ -56,13 +68,28 @@ __device__ __forceinline__ void account(const ValArgs& a, int32_t v, int32_t cv,
     else if (cv >= kPresColors) atomicAdd(&a.c->big_colors, 1);
 }
 
+// One piece of a row: its same-colored neighbors; the row's own accounting
+// (uncolored, max color, presence) with its first piece only.
+__device__ __forceinline__ void account_piece(const ValArgs& a, int32_t v, int32_t cv, int32_t same, bool first,
+                                              uint32_t* s_pres, unsigned long long& conf,
+                                              unsigned long long& unc, int32_t& my_max) {
+    if (first) {
+        account(a, v, cv, same, s_pres, conf, unc, my_max);
+        return;
+    }
+    conf += static_cast<unsigned long long>(same);
+    if (same > 0) atomicMin(&a.c->first_bad, static_cast<long long>(v));
+}
+
 __device__ __forceinline__ void flush_presence(const ValArgs& a, uint32_t* s_pres) {
     __syncthreads();
     for (int i = threadIdx.x; i < kPresWords; i += kBlock)
         if (s_pres[i]) atomicOr(&a.pres[i], s_pres[i]);
 }
 
-// Light rows: kValG lanes per vertex; heavy rows are listed for the next pass.
+// Light rows: kValG lanes per vertex; longer rows are listed for the next
+// pass, from the front of `heavy` up to kValWarpDeg entries, from the back
+// beyond.
 __global__ void __launch_bounds__(kBlock) k_validate(ValArgs a) {
     __shared__ uint32_t s_pres[kPresWords];
     for (int i = threadIdx.x; i < kPresWords; i += kBlock) s_pres[i] = 0u;
@@ -80,14 +107,20 @@ __global__ void __launch_bounds__(kBlock) k_validate(ValArgs a) {
         if (valid) {
             row_of(a.g, static_cast<int32_t>(v), beg, deg, &a.c->err);
             cv = a.colors[v];
-            heavy = deg > kHeavyDeg;
+            heavy = deg > kValLightDeg;
         }
         int32_t same = same_color<1>(a, beg, heavy ? 0 : deg, cv, gl, kValG);
 #pragma unroll
         for (int d = kValG / 2; d >= 1; d >>= 1) same += __shfl_xor_sync(kFull, same, d);
         if (valid && gl == 0) {
-            if (heavy) a.heavy[atomicAdd(&a.c->heavy, 1)] = static_cast<int32_t>(v);
-            else account(a, static_cast<int32_t>(v), cv, same, s_pres, conf, unc, my_max);
+            if (!heavy) account(a, static_cast<int32_t>(v), cv, same, s_pres, conf, unc, my_max);
+            else if (deg <= kValWarpDeg) a.heavy[atomicAdd(&a.c->heavy, 1)] = static_cast<int32_t>(v);
+            else {
+                const int32_t np = (deg + kValPiece - 1) / kValPiece;
+                const int32_t p0 = atomicAdd(&a.c->big, np);
+                for (int32_t i = 0; i < np && p0 + i < a.piece_cap; ++i)
+                    a.pieces[p0 + i] = make_int2(static_cast<int32_t>(v), i);
+            }
         }
     }
     warp_add(&a.c->conflicts, conf);
@@ -96,30 +129,47 @@ __global__ void __launch_bounds__(kBlock) k_validate(ValArgs a) {
     flush_presence(a, s_pres);
 }
 
-// Heavy rows: one block per vertex.
+// The rows k_validate listed: a warp each up to kValWarpDeg entries, then a
+// block per piece of kValPiece entries beyond.
 __global__ void __launch_bounds__(kBlock) k_validate_heavy(ValArgs a) {
     __shared__ uint32_t s_pres[kPresWords];
     __shared__ int32_t s_sum[kWarps];
     for (int i = threadIdx.x; i < kPresWords; i += kBlock) s_pres[i] = 0u;
     __syncthreads();
-    const int32_t nh = a.c->heavy;
     int32_t my_max = 0;
     unsigned long long conf = 0, unc = 0;
-    for (int32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+    const int32_t nmid = a.c->heavy, nbig = a.c->big;
+    const int w = threadIdx.x >> 5, l = lane_id();
+    for (int32_t h = blockIdx.x * kWarps + w; h < nmid; h += gridDim.x * kWarps) {
         const int32_t v = a.heavy[h];
         int64_t beg;
         int32_t deg;
         row_of(a.g, v, beg, deg, &a.c->err);
         const int32_t cv = a.colors[v];
-        int32_t same = same_color<1>(a, beg, deg, cv, threadIdx.x, kBlock);
+        int32_t same = same_color<2>(a, beg, deg, cv, l, 32);
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) same += __shfl_xor_sync(kFull, same, d);
+        if (l == 0) account(a, v, cv, same, s_pres, conf, unc, my_max);
+    }
+    const int64_t npieces = nbig < a.piece_cap ? nbig : a.piece_cap;
+    for (int64_t k = blockIdx.x; k < npieces; k += gridDim.x) {
+        const int2 pc = a.pieces[k];
+        const int32_t v = pc.x;
+        int64_t beg;
+        int32_t deg;
+        row_of(a.g, v, beg, deg, &a.c->err);
+        const int64_t off = static_cast<int64_t>(pc.y) * kValPiece;
+        const int32_t len = static_cast<int32_t>(min(static_cast<int64_t>(kValPiece), deg - off));
+        const int32_t cv = a.colors[v];
+        int32_t same = same_color<1>(a, beg + off, len, cv, threadIdx.x, kBlock);
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) same += __shfl_xor_sync(kFull, same, d);
         if (lane_id() == 0) s_sum[threadIdx.x >> 5] = same;
         __syncthreads();
         if (threadIdx.x == 0) {
             int32_t tot = 0;
-            for (int w = 0; w < kWarps; ++w) tot += s_sum[w];
-            account(a, v, cv, tot, s_pres, conf, unc, my_max);
+            for (int q = 0; q < kWarps; ++q) tot += s_sum[q];
+            account_piece(a, v, cv, tot, pc.y == 0, s_pres, conf, unc, my_max);
         }
         __syncthreads();
     }
@@ -152,10 +202,13 @@ gc_status validate_device(const Graph& g, const int32_t* colors, gc_validation* 
     std::memset(out, 0, sizeof(*out));
     out->first_bad_vertex = -1;
     if (g.n == 0) return GC_OK;
-    Scratch sc, sp, shv;
-    if (!sc.alloc(sizeof(ValCtrl), s) || !sp.alloc(kPresWords * 4, s) || !shv.alloc(static_cast<int64_t>(g.n) * 4, s))
+    Scratch sc, sp, shv, spc;
+    // pieces: at most one per kValPiece entries, plus one per row beyond kValWarpDeg
+    const int64_t piece_cap = g.nnz / kValPiece + g.nnz / kValWarpDeg + 1;
+    if (!sc.alloc(sizeof(ValCtrl), s) || !sp.alloc(kPresWords * 4, s) || !shv.alloc(static_cast<int64_t>(g.n) * 4, s) ||
+        !spc.alloc(piece_cap * sizeof(int2), s))
         return GC_ERR_OOM;
-    ValArgs a{g, colors, sc.as<ValCtrl>(), sp.as<uint32_t>(), shv.as<int32_t>()};
+    ValArgs a{g, colors, sc.as<ValCtrl>(), sp.as<uint32_t>(), shv.as<int32_t>(), spc.as<int2>(), piece_cap};
     ValCtrl h;
     std::memset(&h, 0, sizeof(h));
     h.first_bad = LLONG_MAX;
